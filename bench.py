@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the Sinkhorn-UOT hot path on GB300.
+
+Default workload: one UOT problem N=M=16384 in FP32 (1 GiB plan), C = squared
+distances of standard-Gaussian 64-D clouds divided by max(C), a/b Dirichlet(1)
+times masses 1.0/2.0, reg 0.1, reg_m 0.5, 500 iterations.  A step is the
+whole solve: P0 = exp(-C/reg), 500 fused iteration passes plus the finishing
+sweep, and the FP64 transport cost.  ``value`` counts plan elements processed
+per second (N*M*iters per step) with C, a, b already resident on the GPU;
+``e2e`` repeats the same solve through the public API from pinned host
+buffers (C, a, b copied in, plan and cost copied out inside the timed region).
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead
+(each step is a bounded sample: one oracle iteration on the full-size plan).
+
+Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 run it
+under ``torch.distributed.run`` -- every rank then solves its own problem
+(independent problems, no collective on the data path, weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "UOT Sinkhorn plan elems/s & HBM GB/s vs 8 TB/s; fused/bf16/batched vs plain FP32"
+UNIT = "plan elems/s"
+KERNEL_SOURCES = ["paper_2412_11079_gb300/csrc/fused.cu",
+                  "paper_2412_11079_gb300/csrc/uot_device.cuh",
+                  "paper_2412_11079_gb300/csrc/uot_internal.h"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_pass_traffic.json")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if bus_id:
+                cmd += ["-i", bus_id]
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) == 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def bus_id_of(torch, dev):
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+def make_problem(seed: int, args):
+    from paper_2412_11079_gb300 import workloads
+    return workloads.large_case(seed=seed, n=args.n, m=args.m, iters=args.iters)
+
+
+def oracle_rate(p, iters: int):
+    """FP64 oracle: plan elems/s over `iters` iterations of the full plan."""
+    import oracle
+    P = oracle.init_plan(p.C, p.reg)
+    t0 = time.perf_counter()
+    oracle.sinkhorn(P, p.a, p.b, p.reg, p.reg_m, iters)
+    dt = time.perf_counter() - t0
+    return p.C.size * iters / dt, dt
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    p = make_problem(0, args)
+    import oracle
+    P = oracle.init_plan(p.C, p.reg)
+    for _ in range(args.warmup):
+        P = oracle.sinkhorn(P, p.a, p.b, p.reg, p.reg_m, 1).plan
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P = oracle.sinkhorn(P, p.a, p.b, p.reg, p.reg_m, 1).plan
+    dt = time.perf_counter() - t0
+    value = p.C.size * args.steps / dt
+    sample = (f"{args.steps} oracle iterations (1 per step) on the full {args.n}x{args.m} "
+              f"plan, FP64 numpy, after {args.warmup} warm-up iterations")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args):
+    return {"workload": f"single UOT problem N=M={args.n}" if args.n == args.m else
+            f"single UOT problem {args.n}x{args.m}",
+            "n": args.n, "m": args.m, "iters": args.iters, "reg": 0.1, "reg_m": 0.5,
+            "cost": "squared distances of N(0, I_64) clouds / max",
+            "marginals": "Dirichlet(1) x 1.0 / x 2.0", "plan_dtype": "f32",
+            "algo": "fused one-pass", "l2": "plan (1 GiB) larger than L2, no flush needed"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--m", type=int, default=16384)
+    ap.add_argument("--iters", type=int, default=500)
+    ap.add_argument("--oracle-iters", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_11079_gb300 import build, uot
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    uot.load()
+
+    p = make_problem(rank, args)
+    n, m, iters = args.n, args.m, args.iters
+    stream = torch.cuda.current_stream(dev)
+    C = torch.from_numpy(p.C).to(dev)
+    a = torch.from_numpy(p.a).to(dev)
+    b = torch.from_numpy(p.b).to(dev)
+    plan = torch.empty((n, m), dtype=torch.float32, device=dev)
+    cost = torch.empty(1, dtype=torch.float64, device=dev)
+    opt = uot.options()
+    ws = uot.workspace(n, m, opt, dev)
+
+    def step(o):
+        uot.uot_init_kernel(C, plan, p.reg, opt, stream)
+        uot.uot_sinkhorn(plan, a, b, p.reg, p.reg_m, iters, 0.0, ws, o, stream, sync=False)
+        uot.uot_cost(plan, C, cost, stream)
+
+    for _ in range(args.warmup):
+        step(opt)
+    torch.cuda.synchronize()
+    res = uot.uot_read_result(ws, n, m, opt)
+    if res.dev_status != 0 or res.iters_done != iters:
+        raise RuntimeError(f"solve failed: {res}")
+
+    # Timed region: K steps, CUDA events on the launching stream; the fused
+    # passes of each step are bracketed by their own event pair.
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    opts = []
+    for e0, e1 in evs:
+        e0.record(stream)  # torch creates the underlying cudaEvent on first record
+        e1.record(stream)
+        o = uot.options()
+        o.pass_events[0] = e0.cuda_event
+        o.pass_events[1] = e1.cuda_event
+        opts.append(o)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(bus_id_of(torch, dev)) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0.0)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = uot.uot_launch_count()
+    start.record(stream)
+    for k in range(args.steps):
+        step(opts[k])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    launches = uot.uot_launch_count() - launches0
+    clocks = sampler.stop() if sampler else None
+    elapsed_ms = start.elapsed_time(stop)
+    pass_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = t.item()
+        dist.barrier()
+    ms_step = elapsed_ms / args.steps
+    elems = float(n) * m * iters * args.steps * world
+    value = elems / (elapsed_ms * 1e-3)
+    res = uot.uot_read_result(ws, n, m, opt)
+    assert res.dev_status == 0 and res.iters_done == iters
+
+    # Roofline of the dominant kernel (the fused pass): algorithmic bytes per
+    # launch = one read and one write of the FP32 plan = 8*N*M.
+    per_launch_s = pass_ms * 1e-3 / (args.steps * iters)
+    alg_bytes = 8.0 * n * m
+    achieved = alg_bytes / per_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as fh:
+            tr = json.load(fh)
+        if tr.get("source_hash") == kernel_hash():
+            traffic = tr["bytes_per_elem"] * n * m
+
+    # End to end through the public API from pinned host buffers.
+    hC = torch.from_numpy(p.C).pin_memory()
+    ha = torch.from_numpy(p.a).pin_memory()
+    hb = torch.from_numpy(p.b).pin_memory()
+    hplan = torch.empty((n, m), dtype=torch.float32).pin_memory()
+    hcost = torch.empty(1, dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+
+    def e2e_step():
+        C.copy_(hC, non_blocking=True)
+        a.copy_(ha, non_blocking=True)
+        b.copy_(hb, non_blocking=True)
+        step(opt)
+        hplan.copy_(plan, non_blocking=True)
+        hcost.copy_(cost, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    s1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = s0.elapsed_time(s1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = t.item()
+    e2e_value = float(n) * m * iters * e2e_steps * world / (e2e_ms * 1e-3)
+    h2d = hC.numel() * 4 + ha.numel() * 4 + hb.numel() * 4
+    d2h = hplan.numel() * 4 + 8
+
+    compare = None
+    if not args.no_compare and rank == 0:
+        # Plain multi-pass FP32 on the same GPU and problem (3 reads + 2 writes
+        # + 1 read of the plan per iteration), two steps.
+        mo = uot.options(algo=uot.UOT_ALGO_MULTIPASS)
+        mp_iters = min(iters, 100)
+        uot.uot_init_kernel(C, plan, p.reg, mo, stream)
+        uot.uot_sinkhorn(plan, a, b, p.reg, p.reg_m, mp_iters, 0.0, ws, mo, stream, sync=False)
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(2):
+            uot.uot_sinkhorn(plan, a, b, p.reg, p.reg_m, mp_iters, 0.0, ws, mo, stream, sync=False)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        mp_value = float(n) * m * mp_iters * 2 / (q0.elapsed_time(q1) * 1e-3)
+        compare = {"plain_fp32_multipass": {"value": mp_value, "unit": UNIT,
+                                            "iters": mp_iters},
+                   "fused_over_multipass": value / world / mp_value}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, dt = oracle_rate(p, args.oracle_iters)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.oracle_iters} of {iters} iterations of the FP64 numpy oracle "
+                         f"on the full {n}x{m} plan ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": config_of(args),
+            "hbm_gbs_algorithmic": alg_bytes * iters * args.steps * world
+            / (elapsed_ms * 1e-3) / 1e9,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind, "kernel": "fused_pass_kernel<float,512,8>",
+                         "frac_of_8TBs": achieved / 8000.0,
+                         "launch_ms": per_launch_s * 1e3},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "gpu_launches": launches, "clocks": clocks, "compare": compare,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * uot.h -- C ABI of libuot, the GB300 (sm_103a) Sinkhorn iteration for
+ * entropy-regularised unbalanced optimal transport (MAP-UOT).
+ *
+ * The method (Section 2.1): given a non-negative N x M matrix P and targets
+ * a (length N, row target) and b (length M, column target), each iteration
+ * rescales every row i by alpha_i = (a_i / sum_j P_ij)^fi and then every
+ * column j by beta_j = (b_j / sum_i P_ij)^fi, with fi = reg_m / (reg_m + reg).
+ * MAP-UOT (Section 4, Algorithm 1) performs one iteration as a single sweep
+ * over the matrix: the pending column factor of the previous iteration and the
+ * row rescaling of the current one are applied to a row while it is on chip,
+ * and the column sums for the next factor are accumulated in the same pass.
+ *
+ * Conventions for every entry point
+ *  - Matrices are dense and row-major with a leading dimension (elements
+ *    between row starts) >= the number of columns.  All array pointers are
+ *    DEVICE pointers owned by the caller unless stated otherwise.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued asynchronously; nothing synchronises unless stated.
+ *  - Nothing is allocated or freed on the device by the library; scratch
+ *    memory is a caller-owned workspace sized by uot_workspace_size().
+ *  - Errors are return codes; nothing is thrown across the ABI.  Argument
+ *    errors are detected on the host before anything is enqueued.  Conditions
+ *    found on the device (zero or non-finite sums) are OR-ed into a status
+ *    word in the workspace and reported through uot_result.
+ *  - The plan dtype is FP32, BF16 or FP16 (uot_dtype); row/column sums and
+ *    factors are always FP32; the transport cost and the stopping error are
+ *    accumulated in FP64.
+ */
+#ifndef UOT_H
+#define UOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum uot_status {
+  UOT_OK = 0,
+  UOT_ERR_INVALID_ARG = 1,  /* bad size, pointer, parameter or alignment      */
+  UOT_ERR_CUDA = 2,         /* a CUDA runtime call failed                      */
+  UOT_ERR_NONFINITE = 3,    /* device saw a non-finite sum or factor           */
+  UOT_ERR_ZERO_SUM = 4,     /* device saw a zero sum with a positive target    */
+  UOT_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                    */
+  UOT_ERR_UNSUPPORTED = 6,  /* valid request this build does not implement     */
+  UOT_ERR_WORKSPACE = 7     /* workspace NULL, too small or misaligned         */
+} uot_status;
+
+typedef enum uot_dtype { UOT_F32 = 0, UOT_BF16 = 1, UOT_F16 = 2 } uot_dtype;
+
+/* How uot_sinkhorn sweeps the plan.
+ * FUSED:     one read and one write of the plan per iteration (Algorithm 1's
+ *            single double loop, Section 4.1.1), the default.
+ * MULTIPASS: the separate row-sum, row-scale, column-sum and column-scale
+ *            sweeps of the baseline form of Section 2.1 (three reads and two
+ *            writes of the plan per iteration plus one more read), kept as the
+ *            plain GPU reference the fused path is compared against. */
+typedef enum uot_algo { UOT_ALGO_FUSED = 0, UOT_ALGO_MULTIPASS = 1 } uot_algo;
+
+/* Bits of uot_result.dev_status. */
+#define UOT_DEV_ZERO_SUM 1u
+#define UOT_DEV_NONFINITE 2u
+#define UOT_DEV_TIMEOUT 4u
+
+typedef struct uot_options {
+  int32_t dtype;        /* uot_dtype of the plan storage (default UOT_F32)    */
+  int32_t algo;         /* uot_algo (default UOT_ALGO_FUSED)                  */
+  int32_t check_every;  /* stopping-rule period in iterations, >= 1           */
+  int32_t tile;         /* 0 = automatic; k > 0 forces fused config k-1 of
+                           uot_fused_config() (for tuning and tests)          */
+  int32_t cluster;      /* 0 = automatic; else CTAs per row (1..8), fused only */
+  int32_t reserved[3];  /* must be 0                                          */
+  void* pass_events[2]; /* optional cudaEvent_t pair: uot_sinkhorn records
+                           [0] on `stream` just before its first iteration
+                           pass and [1] just after its last (NULL = none);
+                           used to time the passes alone                     */
+} uot_options;
+
+typedef struct uot_result {
+  int32_t iters_done;   /* iterations completed (< iters if tol stopped it)   */
+  uint32_t dev_status;  /* UOT_DEV_* bits seen on the device                  */
+  double err;           /* last stopping error computed, or +inf if none      */
+} uot_result;
+
+/* Fills *opt with the defaults above. */
+void uot_default_options(uot_options* opt);
+
+/* Human-readable name of a status code (static string). */
+const char* uot_status_string(uot_status s);
+
+/* Bytes of device workspace uot_sinkhorn needs for an n x m plan (a multiple
+ * of 256).  The workspace must be 256-byte aligned.  Returns 0 on bad sizes. */
+size_t uot_workspace_size(int64_t n, int64_t m, const uot_options* opt);
+
+/* Number of kernels this library has launched in the calling process (a
+ * monotone counter, for accounting in benchmarks). */
+uint64_t uot_launch_count(void);
+
+/*
+ * uot_init_kernel -- initial plan P0_ij = exp(-C_ij / reg).
+ * Section 2.1 starts from a "given matrix"; the Gibbs kernel of the cost is
+ * the usual one for entropic transport.  C: n x m FP32, leading dimension ldc.
+ * plan: n x m of opt->dtype (FP32 if opt is NULL), leading dimension ldp,
+ * written with round-to-nearest-even.  FP32 expf, no fast-math.
+ * Errors: UOT_ERR_INVALID_ARG (n, m < 1; ld < m; reg not > 0 or not finite;
+ * NULL pointers), UOT_ERR_CUDA.
+ */
+uot_status uot_init_kernel(const float* C, int64_t ldc, void* plan, int64_t ldp,
+                           int64_t n, int64_t m, float reg,
+                           const uot_options* opt, void* stream);
+
+/*
+ * uot_sinkhorn -- `iters` iterations of the Section 2.1 rule on `plan`, in place.
+ * Each iteration: row step (alpha_i = (a_i/r_i)^fi) then column step
+ * (beta_j = (b_j/c_j)^fi); fi = reg_m/(reg_m+reg), reg_m = +INFINITY gives
+ * fi = 1 (balanced Sinkhorn).  The fused algorithm runs one plan sweep per
+ * iteration plus one final sweep that applies the last column factor, so on
+ * return `plan` holds the plan after the column step of the last iteration.
+ * Degenerate factors: target 0 gives factor 0; a zero sum with a positive
+ * target gives factor 1 and UOT_DEV_ZERO_SUM.
+ * Stopping (the paper leaves the error undefined): when tol > 0, after every
+ * check_every-th iteration t >= 2, err_t = sum_i |r_t,i - r_{t-1},i| /
+ * sum_i r_t,i (FP64) is compared with tol and the remaining iterations are
+ * skipped on the device once err_t <= tol (no host synchronisation).
+ *   plan      n x m, dtype opt->dtype, leading dimension ldp, in/out.
+ *   a, b      FP32 targets of length n and m, read-only, >= 0.
+ *   workspace device scratch of >= uot_workspace_size(n, m, opt) bytes,
+ *             256-byte aligned, owned by the caller; ws_bytes is its size.
+ *             It also holds the result (iterations done, error, status) until
+ *             the next call with the same workspace.
+ *   out       host pointer: if non-NULL the call synchronises `stream` and
+ *             fills *out, returning UOT_ERR_NONFINITE / UOT_ERR_ZERO_SUM /
+ *             UOT_ERR_TIMEOUT if the device flagged one.  If NULL the call is
+ *             fully asynchronous (and may be captured in a CUDA graph); read
+ *             the result later with uot_read_result().
+ * Errors: UOT_ERR_INVALID_ARG, UOT_ERR_WORKSPACE, UOT_ERR_CUDA, device codes.
+ */
+uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b,
+                        int64_t n, int64_t m, float reg, float reg_m,
+                        int32_t iters, double tol, void* workspace, size_t ws_bytes,
+                        const uot_options* opt, void* stream, uot_result* out);
+
+/* Synchronises `stream` and reads the result of the last uot_sinkhorn call
+ * that used `workspace` (same n, m, opt).  Returns the device status as a
+ * uot_status as uot_sinkhorn does with a non-NULL `out`. */
+uot_status uot_read_result(const void* workspace, int64_t n, int64_t m,
+                           const uot_options* opt, void* stream, uot_result* out);
+
+/*
+ * uot_cost -- transport cost <P, C> = sum_ij P_ij C_ij, accumulated in FP64.
+ * plan: n x m of `dtype` (uot_dtype), leading dimension ldp; C: n x m FP32,
+ * leading dimension ldc; out_dev: one device double, OVERWRITTEN with the cost
+ * (the call zeroes it first on `stream`).  Asynchronous.
+ * Errors: UOT_ERR_INVALID_ARG, UOT_ERR_CUDA.
+ */
+uot_status uot_cost(const void* plan, int64_t ldp, const float* C, int64_t ldc,
+                    int64_t n, int64_t m, int32_t dtype, double* out_dev, void* stream);
+
+/* Description of fused-pass configuration k (0-based), for tuning tools:
+ * writes dtype, threads per CTA, 16-byte vectors per thread per row and the
+ * columns one CTA covers.  Returns the number of configurations when k < 0 or
+ * k is out of range (then nothing is written). */
+int32_t uot_fused_config(int32_t k, int32_t* dtype, int32_t* threads,
+                         int32_t* vecs, int32_t* cols_per_cta);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UOT_H */

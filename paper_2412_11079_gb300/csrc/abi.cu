@@ -1,0 +1,234 @@
+// The extern "C" entry points of libuot (declared in include/uot.h): argument
+// validation on the host, workspace layout, and the per-iteration launch
+// sequence of the Sinkhorn-UOT iteration (Section 2.1 / Algorithm 1).
+#include <atomic>
+#include <cmath>
+#include <cstring>
+
+#include <cuda_runtime.h>
+
+#include "uot_internal.h"
+
+namespace uot {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add(uint64_t(k), std::memory_order_relaxed); }
+
+static size_t esize(int dtype) { return dtype == UOT_F32 ? 4 : 2; }
+
+static bool valid_dtype(int d) { return d == UOT_F32 || d == UOT_BF16 || d == UOT_F16; }
+
+static bool valid_dims(int64_t n, int64_t m) {
+  return n >= 1 && m >= 1 && n <= INT32_MAX && m <= INT32_MAX / 2;
+}
+
+static uot_options resolve(const uot_options* opt) {
+  uot_options o;
+  uot_default_options(&o);
+  if (opt) o = *opt;
+  if (o.check_every <= 0) o.check_every = 1;
+  return o;
+}
+
+static bool reserved_zero(const uot_options& o) {
+  for (int k = 0; k < 3; ++k)
+    if (o.reserved[k] != 0) return false;
+  return true;
+}
+
+static uot_status status_of(uint32_t dev) {
+  if (dev & UOT_DEV_TIMEOUT) return UOT_ERR_TIMEOUT;
+  if (dev & UOT_DEV_NONFINITE) return UOT_ERR_NONFINITE;
+  if (dev & UOT_DEV_ZERO_SUM) return UOT_ERR_ZERO_SUM;
+  return UOT_OK;
+}
+
+}  // namespace uot
+
+using namespace uot;
+
+extern "C" {
+
+void uot_default_options(uot_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->dtype = UOT_F32;
+  opt->algo = UOT_ALGO_FUSED;
+  opt->check_every = 1;
+}
+
+const char* uot_status_string(uot_status s) {
+  switch (s) {
+    case UOT_OK: return "ok";
+    case UOT_ERR_INVALID_ARG: return "invalid argument";
+    case UOT_ERR_CUDA: return "CUDA error";
+    case UOT_ERR_NONFINITE: return "non-finite sum or factor on the device";
+    case UOT_ERR_ZERO_SUM: return "zero sum with a positive target on the device";
+    case UOT_ERR_TIMEOUT: return "bounded device wait timed out";
+    case UOT_ERR_UNSUPPORTED: return "unsupported configuration";
+    case UOT_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+  }
+  return "unknown status";
+}
+
+size_t uot_workspace_size(int64_t n, int64_t m, const uot_options* opt) {
+  (void)opt;
+  if (!valid_dims(n, m)) return 0;
+  return ws_layout(n, m).total;
+}
+
+uint64_t uot_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+uot_status uot_init_kernel(const float* C, int64_t ldc, void* plan, int64_t ldp, int64_t n,
+                           int64_t m, float reg, const uot_options* opt, void* stream) {
+  const uot_options o = resolve(opt);
+  if (!C || !plan || !valid_dims(n, m) || ldc < m || ldp < m || !valid_dtype(o.dtype))
+    return UOT_ERR_INVALID_ARG;
+  if (!(reg > 0.0f) || !std::isfinite(reg)) return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(plan) % esize(o.dtype) || reinterpret_cast<uintptr_t>(C) % 4)
+    return UOT_ERR_INVALID_ARG;
+  cudaError_t e = launch_init(C, ldc, plan, ldp, int(n), int(m), reg, o.dtype,
+                              static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? UOT_OK : UOT_ERR_CUDA;
+}
+
+uot_status uot_read_result(const void* workspace, int64_t n, int64_t m, const uot_options* opt,
+                           void* stream, uot_result* out) {
+  (void)opt;
+  if (!workspace || !out || !valid_dims(n, m)) return UOT_ERR_INVALID_ARG;
+  const WsLayout L = ws_layout(n, m);
+  Control ctl;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&ctl, static_cast<const uint8_t*>(workspace) + L.ctl, sizeof(ctl),
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return UOT_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return UOT_ERR_CUDA;
+  out->iters_done = ctl.iters_done;
+  out->dev_status = ctl.status;
+  out->err = ctl.err;
+  return status_of(ctl.status);
+}
+
+uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b, int64_t n,
+                        int64_t m, float reg, float reg_m, int32_t iters, double tol,
+                        void* workspace, size_t ws_bytes, const uot_options* opt, void* stream,
+                        uot_result* out) {
+  const uot_options o = resolve(opt);
+  if (!plan || !a || !b || !valid_dims(n, m) || ldp < m || !valid_dtype(o.dtype))
+    return UOT_ERR_INVALID_ARG;
+  if (!(reg > 0.0f) || !std::isfinite(reg) || !(reg_m > 0.0f) || iters < 0)
+    return UOT_ERR_INVALID_ARG;
+  if (std::isnan(tol) || std::isinf(tol) || !reserved_zero(o)) return UOT_ERR_INVALID_ARG;
+  if (o.algo != UOT_ALGO_FUSED && o.algo != UOT_ALGO_MULTIPASS) return UOT_ERR_INVALID_ARG;
+  if (o.cluster < 0 || o.cluster > 8 || o.tile < 0) return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(plan) % esize(o.dtype) ||
+      reinterpret_cast<uintptr_t>(a) % 4 || reinterpret_cast<uintptr_t>(b) % 4)
+    return UOT_ERR_INVALID_ARG;
+  const WsLayout L = ws_layout(n, m);
+  if (!workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(workspace) % 256)
+    return UOT_ERR_WORKSPACE;
+
+  const double fi_d = std::isinf(reg_m) ? 1.0 : double(reg_m) / (double(reg_m) + double(reg));
+  const float fi = float(fi_d);
+  const bool track = tol > 0.0;
+  if (o.algo == UOT_ALGO_MULTIPASS && track) return UOT_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  const int N = int(n), M = int(m);
+
+  // Fused-pass geometry, validated before anything is enqueued.
+  int k = -1, cs = 1, grid = 0, stages = 0;
+  size_t smem = 0;
+  if (o.algo == UOT_ALGO_FUSED && iters > 0) {
+    k = fused_pick(o.dtype, m, o.tile);
+    if (k < 0) return UOT_ERR_INVALID_ARG;
+    FusedConfig cfg;
+    fused_config_info(k, &cfg);
+    cs = o.cluster > 0 ? o.cluster : int((m + cfg.cols - 1) / cfg.cols);
+    if (cs > 8) return UOT_ERR_UNSUPPORTED;
+    if (int64_t(cs) * cfg.cols < m) return UOT_ERR_INVALID_ARG;
+    if (fused_geometry(k, cs, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
+  }
+
+  if (launch_reset(ws, L, s) != cudaSuccess) return UOT_ERR_CUDA;
+  cudaEvent_t ev0 = static_cast<cudaEvent_t>(o.pass_events[0]);
+  cudaEvent_t ev1 = static_cast<cudaEvent_t>(o.pass_events[1]);
+  if (ev0 && cudaEventRecord(ev0, s) != cudaSuccess) return UOT_ERR_CUDA;
+
+  if (o.algo == UOT_ALGO_MULTIPASS) {
+    for (int t = 1; t <= iters; ++t) {
+      if (launch_multipass_iter(plan, ldp, N, M, o.dtype, a, b, fi, t, tol, o.check_every, ws, L,
+                                s, nullptr) != cudaSuccess)
+        return UOT_ERR_CUDA;
+    }
+    if (ev1 && cudaEventRecord(ev1, s) != cudaSuccess) return UOT_ERR_CUDA;
+  } else if (iters == 0) {
+    if (ev1 && cudaEventRecord(ev1, s) != cudaSuccess) return UOT_ERR_CUDA;
+  } else {
+    const bool tma = reinterpret_cast<uintptr_t>(plan) % 16 == 0 &&
+                     (uint64_t(ldp) * esize(o.dtype)) % 16 == 0;
+
+    FusedArgs A{};
+    A.plan = plan;
+    A.ldp = ldp;
+    A.n = N;
+    A.m = M;
+    A.a = a;
+    A.b = b;
+    A.fi = fi;
+    A.track = track ? 1 : 0;
+    A.tol = tol;
+    A.mpad = int(L.mpad);
+    A.r_prev = reinterpret_cast<float*>(ws + L.r);
+    A.ctl = reinterpret_cast<Control*>(ws + L.ctl);
+    A.stages = stages;
+    float* c[3];
+    double* er[3];
+    for (int q = 0; q < 3; ++q) {
+      c[q] = reinterpret_cast<float*>(ws + L.c[q]);
+      er[q] = reinterpret_cast<double*>(ws + L.err) + 2 * q;
+    }
+    for (int t = 1; t <= iters; ++t) {
+      A.t = t;
+      A.first = t == 1;
+      A.check_prev = track && (t - 1) >= 2 && ((t - 1) % o.check_every) == 0;
+      A.c_prev = c[(t - 1) % 3];
+      A.c_next = c[t % 3];
+      A.c_clear = c[(t + 1) % 3];
+      A.err_prev = er[(t - 1) % 3];
+      A.err_next = er[t % 3];
+      A.err_clear = er[(t + 1) % 3];
+      if (fused_launch(k, cs, grid, smem, tma, A, s) != cudaSuccess) return UOT_ERR_CUDA;
+    }
+    if (ev1 && cudaEventRecord(ev1, s) != cudaSuccess) return UOT_ERR_CUDA;
+    if (launch_finish(plan, ldp, N, M, o.dtype, b, fi, iters, ws, L, tol, o.check_every, s) !=
+        cudaSuccess)
+      return UOT_ERR_CUDA;
+  }
+  if (!out) return UOT_OK;
+  return uot_read_result(workspace, n, m, &o, stream, out);
+}
+
+uot_status uot_cost(const void* plan, int64_t ldp, const float* C, int64_t ldc, int64_t n,
+                    int64_t m, int32_t dtype, double* out_dev, void* stream) {
+  if (!plan || !C || !out_dev || !valid_dims(n, m) || ldp < m || ldc < m || !valid_dtype(dtype))
+    return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(plan) % esize(dtype) || reinterpret_cast<uintptr_t>(out_dev) % 8)
+    return UOT_ERR_INVALID_ARG;
+  cudaError_t e = launch_cost(plan, ldp, C, ldc, int(n), int(m), dtype, out_dev,
+                              static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? UOT_OK : UOT_ERR_CUDA;
+}
+
+int32_t uot_fused_config(int32_t k, int32_t* dtype, int32_t* threads, int32_t* vecs,
+                         int32_t* cols_per_cta) {
+  FusedConfig c;
+  if (k < 0 || !fused_config_info(k, &c)) return fused_num_configs();
+  if (dtype) *dtype = c.dtype;
+  if (threads) *threads = c.threads;
+  if (vecs) *vecs = c.vecs;
+  if (cols_per_cta) *cols_per_cta = c.cols;
+  return fused_num_configs();
+}
+
+}  // extern "C"

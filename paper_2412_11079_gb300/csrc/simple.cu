@@ -1,0 +1,272 @@
+// Simple streaming kernels of libuot: the initial plan, the finishing sweep
+// that applies the last pending column factor, the transport cost, the
+// workspace reset, and the plain multi-pass form of one iteration (separate
+// row-sum, row-scale, column-sum and column-scale sweeps, the baseline form
+// of Section 2.1 that Section 3.1 analyses).
+#include <cuda_runtime.h>
+
+#include "uot_device.cuh"
+#include "uot_internal.h"
+
+namespace uot {
+
+namespace {
+
+constexpr int TB = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(TB) init_kernel(const float* __restrict__ C, int64_t ldc,
+                                                  T* __restrict__ P, int64_t ldp, int n, int m,
+                                                  float reg) {
+  const int j = blockIdx.x * TB + threadIdx.x;
+  if (j >= m) return;
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    const float c = C[int64_t(i) * ldc + j];
+    Elem<T>::store1(P + int64_t(i) * ldp + j, expf(-c / reg));
+  }
+}
+
+// Applies beta_j = (b_j / c_j)^fi of the last completed iteration and records
+// the iteration count and the last stopping error.
+template <typename T>
+__global__ void __launch_bounds__(TB) finish_kernel(T* __restrict__ P, int64_t ldp, int n, int m,
+                                                    const float* __restrict__ b, float fi,
+                                                    int iters, const float* c0, const float* c1,
+                                                    const float* c2, const double* err_ring,
+                                                    Control* ctl, double tol, int check_every) {
+  const int done = ctl->done;
+  const int t = done ? ctl->stop_iter : iters;
+  const float* c = (t % 3 == 0) ? c0 : (t % 3 == 1) ? c1 : c2;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    ctl->iters_done = t;
+    if (!done && tol > 0.0 && t >= 2) {
+      const double num = err_ring[(t % 3) * 2], den = err_ring[(t % 3) * 2 + 1];
+      ctl->err = den > 0.0 ? num / den : __longlong_as_double(0x7ff0000000000000ll);
+    }
+  }
+  const int j = blockIdx.x * TB + threadIdx.x;
+  if (j >= m) return;
+  uint32_t st = 0;
+  const float beta = rescale_factor(b[j], c[j], fi, st);
+  if (st && blockIdx.y == 0) atomicOr(&ctl->status, st);
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    T* q = P + int64_t(i) * ldp + j;
+    Elem<T>::store1(q, Elem<T>::load1(q) * beta);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TB) cost_kernel(const T* __restrict__ P, int64_t ldp,
+                                                  const float* __restrict__ C, int64_t ldc, int n,
+                                                  int m, double* out) {
+  __shared__ double part[TB / 32];
+  const int j = blockIdx.x * TB + threadIdx.x;
+  double acc = 0.0;
+  if (j < m)
+    for (int i = blockIdx.y; i < n; i += gridDim.y)
+      acc += double(Elem<T>::load1(P + int64_t(i) * ldp + j)) * double(C[int64_t(i) * ldc + j]);
+  acc = warp_sum_d(acc);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < TB / 32; ++w) s += part[w];
+    atomicAdd(out, s);
+  }
+}
+
+__global__ void reset_kernel(Control* ctl, double* err_ring, float* c1, int mpad) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g == 0) {
+    ctl->status = 0;
+    ctl->done = 0;
+    ctl->stop_iter = 0;
+    ctl->iters_done = 0;
+    ctl->err = __longlong_as_double(0x7ff0000000000000ll);
+  }
+  if (g < 6) err_ring[g] = 0.0;
+  for (int j = g; j < mpad; j += gridDim.x * blockDim.x) c1[j] = 0.0f;
+}
+
+// ---- multi-pass iteration: 5 launches, 3 reads + 2 writes of the plan ----
+
+// One warp per row: r_i = sum_j P_ij, f_i = (a_i / r_i)^fi.  Also clears the
+// column-sum buffer for this iteration.
+template <typename T>
+__global__ void __launch_bounds__(TB) mp_row_factor(const T* __restrict__ P, int64_t ldp, int n,
+                                                    int m, const float* __restrict__ a, float fi,
+                                                    float* f, float* c, int mpad, Control* ctl) {
+  const int g = blockIdx.x * TB + threadIdx.x;
+  for (int j = g; j < mpad; j += gridDim.x * TB) c[j] = 0.0f;
+  const int warp = g >> 5, lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * TB) >> 5;
+  uint32_t st = 0;
+  for (int i = warp; i < n; i += nw) {
+    const T* row = P + int64_t(i) * ldp;
+    float s = 0.0f;
+    for (int j = lane; j < m; j += 32) s += Elem<T>::load1(row + j);
+    s = warp_sum(s);
+    if (lane == 0) f[i] = rescale_factor(a[i], s, fi, st);
+  }
+  if (st) atomicOr(&ctl->status, st);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TB) mp_scale_rows(T* __restrict__ P, int64_t ldp, int n, int m,
+                                                    const float* __restrict__ f) {
+  const int j = blockIdx.x * TB + threadIdx.x;
+  if (j >= m) return;
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    T* q = P + int64_t(i) * ldp + j;
+    Elem<T>::store1(q, Elem<T>::load1(q) * f[i]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TB) mp_col_sums(const T* __restrict__ P, int64_t ldp, int n,
+                                                  int m, float* c) {
+  const int j = blockIdx.x * TB + threadIdx.x;
+  if (j >= m) return;
+  float s = 0.0f;
+  for (int i = blockIdx.y; i < n; i += gridDim.y) s += Elem<T>::load1(P + int64_t(i) * ldp + j);
+  atomicAdd(c + j, s);
+}
+
+__global__ void __launch_bounds__(TB) mp_col_factor(const float* __restrict__ b, const float* c,
+                                                    float fi, float* g, int m, Control* ctl) {
+  const int j = blockIdx.x * TB + threadIdx.x;
+  if (j >= m) return;
+  uint32_t st = 0;
+  g[j] = rescale_factor(b[j], c[j], fi, st);
+  if (st) atomicOr(&ctl->status, st);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TB) mp_scale_cols(T* __restrict__ P, int64_t ldp, int n, int m,
+                                                    const float* __restrict__ g, Control* ctl,
+                                                    int t) {
+  const int j = blockIdx.x * TB + threadIdx.x;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ctl->iters_done = t;
+  if (j >= m) return;
+  const float gj = g[j];
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    T* q = P + int64_t(i) * ldp + j;
+    Elem<T>::store1(q, Elem<T>::load1(q) * gj);
+  }
+}
+
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// 2-D grid for the column-parallel kernels: blockIdx.x over columns,
+// blockIdx.y over row strides, about 8 resident CTAs per SM in total.
+dim3 col_grid(int n, int m) {
+  const int gx = (m + TB - 1) / TB;
+  int gy = (sm_count() * 8 + gx - 1) / gx;
+  if (gy > n) gy = n;
+  if (gy > 65535) gy = 65535;
+  if (gy < 1) gy = 1;
+  return dim3(gx, gy, 1);
+}
+
+template <typename F>
+cudaError_t by_dtype(int dtype, F&& f) {
+  switch (dtype) {
+    case UOT_F32: return f(float());
+    case UOT_BF16: return f(__nv_bfloat16());
+    case UOT_F16: return f(__half());
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t last(int k = 1) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) count_launch(k);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t launch_init(const float* C, int64_t ldc, void* P, int64_t ldp, int n, int m,
+                        float reg, int dtype, cudaStream_t s) {
+  return by_dtype(dtype, [&](auto z) {
+    using T = decltype(z);
+    init_kernel<T><<<col_grid(n, m), TB, 0, s>>>(C, ldc, reinterpret_cast<T*>(P), ldp, n, m, reg);
+    return last();
+  });
+}
+
+cudaError_t launch_finish(void* P, int64_t ldp, int n, int m, int dtype, const float* b, float fi,
+                          int iters, const uint8_t* ws, WsLayout L, double tol, int check_every,
+                          cudaStream_t s) {
+  uint8_t* w = const_cast<uint8_t*>(ws);
+  return by_dtype(dtype, [&](auto z) {
+    using T = decltype(z);
+    finish_kernel<T><<<col_grid(n, m), TB, 0, s>>>(
+        reinterpret_cast<T*>(P), ldp, n, m, b, fi, iters, reinterpret_cast<const float*>(w + L.c[0]),
+        reinterpret_cast<const float*>(w + L.c[1]), reinterpret_cast<const float*>(w + L.c[2]),
+        reinterpret_cast<const double*>(w + L.err), reinterpret_cast<Control*>(w + L.ctl), tol,
+        check_every);
+    return last();
+  });
+}
+
+cudaError_t launch_cost(const void* P, int64_t ldp, const float* C, int64_t ldc, int n, int m,
+                        int dtype, double* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  return by_dtype(dtype, [&](auto z) {
+    using T = decltype(z);
+    cost_kernel<T><<<col_grid(n, m), TB, 0, s>>>(reinterpret_cast<const T*>(P), ldp, C, ldc, n, m,
+                                                 out);
+    return last();
+  });
+}
+
+cudaError_t launch_reset(uint8_t* ws, WsLayout L, cudaStream_t s) {
+  const int blocks = int((L.mpad + TB - 1) / TB);
+  reset_kernel<<<blocks, TB, 0, s>>>(reinterpret_cast<Control*>(ws + L.ctl),
+                                     reinterpret_cast<double*>(ws + L.err),
+                                     reinterpret_cast<float*>(ws + L.c[1]), int(L.mpad));
+  return last();
+}
+
+cudaError_t launch_multipass_iter(void* P, int64_t ldp, int n, int m, int dtype, const float* a,
+                                  const float* b, float fi, int t, double tol, int check_every,
+                                  uint8_t* ws, WsLayout L, cudaStream_t s, int* launches) {
+  (void)tol;
+  (void)check_every;
+  Control* ctl = reinterpret_cast<Control*>(ws + L.ctl);
+  float* f = reinterpret_cast<float*>(ws + L.f);
+  float* g = reinterpret_cast<float*>(ws + L.g);
+  float* c = reinterpret_cast<float*>(ws + L.c[0]);
+  return by_dtype(dtype, [&](auto z) {
+    using T = decltype(z);
+    T* plan = reinterpret_cast<T*>(P);
+    const int rows_blocks = sm_count() * 8;
+    mp_row_factor<T><<<rows_blocks, TB, 0, s>>>(plan, ldp, n, m, a, fi, f, c, int(L.mpad), ctl);
+    cudaError_t e = last();
+    if (e != cudaSuccess) return e;
+    const dim3 gg = col_grid(n, m);
+    mp_scale_rows<T><<<gg, TB, 0, s>>>(plan, ldp, n, m, f);
+    if ((e = last()) != cudaSuccess) return e;
+    mp_col_sums<T><<<gg, TB, 0, s>>>(plan, ldp, n, m, c);
+    if ((e = last()) != cudaSuccess) return e;
+    mp_col_factor<<<(m + TB - 1) / TB, TB, 0, s>>>(b, c, fi, g, m, ctl);
+    if ((e = last()) != cudaSuccess) return e;
+    mp_scale_cols<T><<<gg, TB, 0, s>>>(plan, ldp, n, m, g, ctl, t);
+    e = last();
+    if (launches) *launches += 5;
+    return e;
+  });
+}
+
+}  // namespace uot

@@ -1,0 +1,117 @@
+// Internal declarations of libuot shared by its translation units: the
+// workspace layout, kernel argument blocks and the launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/uot.h"
+
+namespace uot {
+
+constexpr uint32_t DEV_ZERO_SUM = UOT_DEV_ZERO_SUM;
+constexpr uint32_t DEV_NONFINITE = UOT_DEV_NONFINITE;
+constexpr uint32_t DEV_TIMEOUT = UOT_DEV_TIMEOUT;
+
+// A bounded device wait gives up after this long (nanoseconds).
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
+
+// Control block at the start of the workspace.
+struct Control {
+  uint32_t status;     // DEV_* bits
+  int32_t done;        // 1 once the stopping rule fired
+  int32_t stop_iter;   // iteration at which it fired
+  int32_t iters_done;  // written by the finishing sweep
+  double err;          // last stopping error (+inf if none)
+  double pad[5];
+};
+
+// Offsets (bytes) of the workspace regions for an n x m problem.
+struct WsLayout {
+  size_t ctl;     // Control
+  size_t err;     // double[3][2]: per-pass (sum |r_t - r_{t-1}|, sum r_t), ring of 3
+  size_t c[3];    // float[mpad]: column sums, ring of 3 (read / accumulate / clear)
+  size_t r;       // float[npad]: previous row sums (stopping rule)
+  size_t f;       // float[npad]: row factors (multi-pass algorithm)
+  size_t g;       // float[mpad]: column factors (multi-pass algorithm)
+  size_t total;
+  int64_t mpad, npad;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+inline WsLayout ws_layout(int64_t n, int64_t m) {
+  WsLayout L{};
+  L.mpad = (m + 63) & ~int64_t(63);
+  L.npad = (n + 63) & ~int64_t(63);
+  size_t off = 0;
+  L.ctl = off; off = align256(off + sizeof(Control));
+  L.err = off; off = align256(off + 6 * sizeof(double));
+  for (int k = 0; k < 3; ++k) { L.c[k] = off; off = align256(off + size_t(L.mpad) * 4); }
+  L.r = off; off = align256(off + size_t(L.npad) * 4);
+  L.f = off; off = align256(off + size_t(L.npad) * 4);
+  L.g = off; off = align256(off + size_t(L.mpad) * 4);
+  L.total = off;
+  return L;
+}
+
+// Arguments of one fused iteration pass.
+struct FusedArgs {
+  void* plan;
+  int64_t ldp;
+  int n, m;
+  const float* a;
+  const float* b;
+  float fi;
+  int t;               // 1-based iteration index of this pass
+  int first;           // 1: no pending column factor (beta = 1)
+  int track;           // 1: record row sums and the stopping-error sums
+  int check_prev;      // 1: test the stopping rule on iteration t-1 first
+  double tol;
+  const float* c_prev; // column sums of iteration t-1 (pending beta)
+  float* c_next;       // column sums of iteration t (accumulated, pre-zeroed)
+  float* c_clear;      // buffer to clear for iteration t+1
+  int mpad;
+  float* r_prev;       // row sums of iteration t-1 -> overwritten with r_t
+  const double* err_prev;
+  double* err_next;
+  double* err_clear;
+  Control* ctl;
+  int stages;          // ring depth
+};
+
+struct FusedConfig {
+  int dtype;
+  int threads;
+  int vecs;     // 16-byte vectors per thread per row
+  int cols;     // columns per CTA
+  int max_regs_ok;
+};
+
+int fused_num_configs();
+bool fused_config_info(int k, FusedConfig* out);
+// Picks a configuration for dtype/m (tile = 0: automatic; else k+1).
+int fused_pick(int dtype, int64_t m, int tile);
+// Launch geometry for config k at cluster size cs: grid (CTAs), ring depth and
+// dynamic shared memory; returns cudaSuccess or an error.
+cudaError_t fused_geometry(int k, int cs, int n, int* grid, int* stages, size_t* smem);
+cudaError_t fused_launch(int k, int cs, int grid, size_t smem, bool tma, const FusedArgs& args,
+                         cudaStream_t s);
+
+// Simple kernels (simple.cu).
+cudaError_t launch_init(const float* C, int64_t ldc, void* P, int64_t ldp, int n, int m,
+                        float reg, int dtype, cudaStream_t s);
+cudaError_t launch_finish(void* P, int64_t ldp, int n, int m, int dtype, const float* b,
+                          float fi, int iters, const uint8_t* ws, WsLayout L, double tol,
+                          int check_every, cudaStream_t s);
+cudaError_t launch_cost(const void* P, int64_t ldp, const float* C, int64_t ldc, int n, int m,
+                        int dtype, double* out, cudaStream_t s);
+cudaError_t launch_reset(uint8_t* ws, WsLayout L, cudaStream_t s);
+cudaError_t launch_multipass_iter(void* P, int64_t ldp, int n, int m, int dtype, const float* a,
+                                  const float* b, float fi, int t, double tol, int check_every,
+                                  uint8_t* ws, WsLayout L, cudaStream_t s, int* launches);
+
+void count_launch(int k = 1);
+
+}  // namespace uot

@@ -1,0 +1,256 @@
+"""Thin ctypes binding of libuot (include/uot.h).
+
+Functions carry the C names and only marshal arguments: torch tensors supply
+device pointers, leading dimensions and the current CUDA stream; every step of
+the iteration runs in the library's CUDA kernels.  There is no fallback: if
+``libuot.so`` is missing or no GPU is present the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libuot.so")
+
+UOT_OK = 0
+UOT_ERR_INVALID_ARG = 1
+UOT_ERR_CUDA = 2
+UOT_ERR_NONFINITE = 3
+UOT_ERR_ZERO_SUM = 4
+UOT_ERR_TIMEOUT = 5
+UOT_ERR_UNSUPPORTED = 6
+UOT_ERR_WORKSPACE = 7
+
+UOT_F32, UOT_BF16, UOT_F16 = 0, 1, 2
+UOT_ALGO_FUSED, UOT_ALGO_MULTIPASS = 0, 1
+UOT_DEV_ZERO_SUM, UOT_DEV_NONFINITE, UOT_DEV_TIMEOUT = 1, 2, 4
+
+
+class UotOptions(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("algo", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("cluster", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+                ("pass_events", ctypes.c_void_p * 2)]
+
+
+class UotResult(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int32), ("dev_status", ctypes.c_uint32),
+                ("err", ctypes.c_double)]
+
+
+class UotError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {uot_status_string(status)} (status {status})")
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported symbol declared in include/uot.h.
+_P, _I64, _I32, _F, _D, _SZ = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                               ctypes.c_float, ctypes.c_double, ctypes.c_size_t)
+SIGNATURES = {
+    "uot_default_options": (None, [ctypes.POINTER(UotOptions)]),
+    "uot_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "uot_workspace_size": (_SZ, [_I64, _I64, ctypes.POINTER(UotOptions)]),
+    "uot_launch_count": (ctypes.c_uint64, []),
+    "uot_init_kernel": (ctypes.c_int, [_P, _I64, _P, _I64, _I64, _I64, _F,
+                                       ctypes.POINTER(UotOptions), _P]),
+    "uot_sinkhorn": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _D, _P, _SZ,
+                                    ctypes.POINTER(UotOptions), _P, ctypes.POINTER(UotResult)]),
+    "uot_read_result": (ctypes.c_int, [_P, _I64, _I64, ctypes.POINTER(UotOptions), _P,
+                                       ctypes.POINTER(UotResult)]),
+    "uot_cost": (ctypes.c_int, [_P, _I64, _P, _I64, _I64, _I64, _I32, _P, _P]),
+    "uot_fused_config": (_I32, [_I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Loads libuot.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libuot.so not found at {path}; build it with "
+                           "paper_2412_11079_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def uot_status_string(status: int) -> str:
+    return load().uot_status_string(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != UOT_OK:
+        raise UotError(status, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(t) -> int:
+    torch = _torch()
+    codes = {torch.float32: UOT_F32, torch.bfloat16: UOT_BF16, torch.float16: UOT_F16}
+    if t not in codes:
+        raise TypeError(f"unsupported plan dtype {t}")
+    return codes[t]
+
+
+def _matrix(x, name):
+    if not x.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if x.dim() != 2 or (x.shape[1] > 1 and x.stride(1) != 1) or x.stride(0) < x.shape[1]:
+        raise ValueError(f"{name} must be a row-major 2-D tensor (unit column stride)")
+    return x.data_ptr(), int(x.stride(0))
+
+
+def _vector(x, name, length):
+    torch = _torch()
+    if not x.is_cuda or x.dtype != torch.float32 or x.dim() != 1 or x.numel() != length:
+        raise ValueError(f"{name} must be a CUDA float32 vector of length {length}")
+    if length > 1 and x.stride(0) != 1:
+        raise ValueError(f"{name} must be contiguous")
+    return x.data_ptr()
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def options(dtype: int = UOT_F32, algo: int = UOT_ALGO_FUSED, check_every: int = 1,
+            tile: int = 0, cluster: int = 0) -> UotOptions:
+    o = UotOptions()
+    load().uot_default_options(ctypes.byref(o))
+    o.dtype, o.algo, o.check_every, o.tile, o.cluster = dtype, algo, check_every, tile, cluster
+    return o
+
+
+def uot_workspace_size(n: int, m: int, opt: UotOptions | None = None) -> int:
+    return int(load().uot_workspace_size(n, m, ctypes.byref(opt) if opt else None))
+
+
+def uot_launch_count() -> int:
+    return int(load().uot_launch_count())
+
+
+def uot_fused_config(k: int):
+    d, t, v, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    total = load().uot_fused_config(k, ctypes.byref(d), ctypes.byref(t), ctypes.byref(v),
+                                    ctypes.byref(c))
+    if k < 0 or k >= total:
+        return total, None
+    return total, {"dtype": d.value, "threads": t.value, "vecs": v.value, "cols": c.value}
+
+
+def workspace(n: int, m: int, opt: UotOptions | None = None, device=None):
+    """A caller-owned workspace tensor for uot_sinkhorn (256-byte aligned)."""
+    torch = _torch()
+    size = uot_workspace_size(n, m, opt)
+    if size == 0:
+        raise ValueError("bad problem size")
+    buf = torch.empty(size + 256, dtype=torch.uint8, device=device or "cuda")
+    off = (-buf.data_ptr()) % 256
+    return buf[off:off + size]
+
+
+def uot_init_kernel(C, plan, reg: float, opt: UotOptions | None = None, stream=None):
+    n, m = C.shape
+    if tuple(plan.shape) != (n, m):
+        raise ValueError("plan and C shapes differ")
+    if C.dtype != _torch().float32:
+        raise ValueError("C must be float32")
+    opt = opt or options(dtype_code(plan.dtype))
+    if opt.dtype != dtype_code(plan.dtype):
+        raise ValueError("options dtype does not match the plan tensor")
+    cp, ldc = _matrix(C, "C")
+    pp, ldp = _matrix(plan, "plan")
+    _check(load().uot_init_kernel(cp, ldc, pp, ldp, n, m, reg, ctypes.byref(opt),
+                                  _stream(stream)), "uot_init_kernel")
+
+
+@dataclass
+class SinkhornResult:
+    iters_done: int
+    dev_status: int
+    err: float
+
+
+def uot_sinkhorn(plan, a, b, reg: float, reg_m: float, iters: int, tol: float = 0.0,
+                 ws=None, opt: UotOptions | None = None, stream=None, sync: bool = True,
+                 check_status: bool = True):
+    """Runs ``iters`` iterations in place on ``plan``.  With ``sync`` the call
+    waits and returns a SinkhornResult; otherwise it returns None and the
+    result can be read with ``uot_read_result``."""
+    n, m = plan.shape
+    opt = opt or options(dtype_code(plan.dtype))
+    if opt.dtype != dtype_code(plan.dtype):
+        raise ValueError("options dtype does not match the plan tensor")
+    if ws is None:
+        ws = workspace(n, m, opt, plan.device)
+    pp, ldp = _matrix(plan, "plan")
+    res = UotResult()
+    st = load().uot_sinkhorn(pp, ldp, _vector(a, "a", n), _vector(b, "b", m), n, m,
+                             float(reg), float(reg_m), int(iters), float(tol), ws.data_ptr(),
+                             ws.numel(), ctypes.byref(opt), _stream(stream),
+                             ctypes.byref(res) if sync else None)
+    if not sync:
+        _check(st, "uot_sinkhorn")
+        return None
+    if st not in (UOT_OK, UOT_ERR_NONFINITE, UOT_ERR_ZERO_SUM, UOT_ERR_TIMEOUT) or (
+            check_status and st != UOT_OK):
+        raise UotError(st, "uot_sinkhorn")
+    return SinkhornResult(res.iters_done, res.dev_status, res.err)
+
+
+def uot_read_result(ws, n: int, m: int, opt: UotOptions | None = None, stream=None):
+    res = UotResult()
+    st = load().uot_read_result(ws.data_ptr(), n, m, ctypes.byref(opt) if opt else None,
+                                _stream(stream), ctypes.byref(res))
+    if st not in (UOT_OK, UOT_ERR_NONFINITE, UOT_ERR_ZERO_SUM, UOT_ERR_TIMEOUT):
+        raise UotError(st, "uot_read_result")
+    return SinkhornResult(res.iters_done, res.dev_status, res.err)
+
+
+def uot_cost(plan, C, out=None, stream=None):
+    """Transport cost <P, C> in FP64; returns a one-element CUDA float64 tensor."""
+    torch = _torch()
+    n, m = plan.shape
+    if tuple(C.shape) != (n, m) or C.dtype != torch.float32:
+        raise ValueError("C must be float32 with the plan's shape")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=plan.device)
+    pp, ldp = _matrix(plan, "plan")
+    cp, ldc = _matrix(C, "C")
+    _check(load().uot_cost(pp, ldp, cp, ldc, n, m, dtype_code(plan.dtype), out.data_ptr(),
+                           _stream(stream)), "uot_cost")
+    return out
+
+
+def solve(C, a, b, reg: float, reg_m: float = math.inf, iters: int = 100, tol: float = 0.0,
+          dtype=None, algo: int = UOT_ALGO_FUSED, check_every: int = 1, stream=None):
+    """Convenience: P0 = exp(-C/reg), ``iters`` iterations, cost.  Returns
+    ``(plan, cost_tensor, SinkhornResult)``; all on C's device."""
+    torch = _torch()
+    dtype = dtype or torch.float32
+    n, m = C.shape
+    plan = torch.empty((n, m), dtype=dtype, device=C.device)
+    opt = options(dtype_code(dtype), algo, check_every)
+    uot_init_kernel(C, plan, reg, opt, stream)
+    res = uot_sinkhorn(plan, a, b, reg, reg_m, iters, tol, opt=opt, stream=stream)
+    cost = uot_cost(plan, C, stream=stream)
+    return plan, cost, res

@@ -1,0 +1,126 @@
+"""The C-ABI library builds, loads and exports every symbol include/uot.h
+declares; host-side argument validation returns error codes without a GPU."""
+
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2412_11079_gb300 import build, uot
+    build.build()
+    return uot.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "uot.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(uot_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2412_11079_gb300 import uot
+    names = declared_functions()
+    assert "uot_sinkhorn" in names and "uot_init_kernel" in names and "uot_cost" in names
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in uot.SIGNATURES, f"binding lacks {name}"
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_2412_11079_gb300 import uot
+    assert uot.uot_status_string(0) == "ok"
+    assert "workspace" in uot.uot_status_string(uot.UOT_ERR_WORKSPACE)
+    o = uot.UotOptions()
+    lib.uot_default_options(ctypes.byref(o))
+    assert (o.dtype, o.algo, o.check_every, o.tile, o.cluster) == (0, 0, 1, 0, 0)
+
+
+def test_workspace_size(lib):
+    from paper_2412_11079_gb300 import uot
+    s = uot.uot_workspace_size(16384, 16384)
+    assert s % 256 == 0 and s >= 3 * 16384 * 4 + 16384 * 4
+    assert uot.uot_workspace_size(0, 5) == 0
+    assert uot.uot_workspace_size(5, -1) == 0
+
+
+def test_fused_config_table(lib):
+    from paper_2412_11079_gb300 import uot
+    total, _ = uot.uot_fused_config(-1)
+    assert total >= 7
+    seen = set()
+    for k in range(total):
+        _, c = uot.uot_fused_config(k)
+        elem = 4 if c["dtype"] == 0 else 2
+        assert c["cols"] == c["threads"] * c["vecs"] * (16 // elem)
+        assert c["threads"] % 32 == 0
+        seen.add(c["dtype"])
+    assert seen == {0, 1, 2}
+
+
+def test_argument_validation_needs_no_gpu(lib):
+    from paper_2412_11079_gb300 import uot
+    o = uot.options()
+    P = ctypes.c_void_p(4096)  # never dereferenced: validation fails first
+    res = uot.UotResult()
+    f = lib.uot_sinkhorn
+    # NULL plan
+    assert f(None, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 1 << 20, ctypes.byref(o), None,
+             ctypes.byref(res)) == uot.UOT_ERR_INVALID_ARG
+    # ld < m
+    assert f(P, 3, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 1 << 20, ctypes.byref(o), None,
+             None) == uot.UOT_ERR_INVALID_ARG
+    # reg <= 0, NaN reg, reg_m <= 0, negative iters, NaN tol
+    for reg, reg_m, iters, tol in [(0.0, 1.0, 5, 0.0), (math.nan, 1.0, 5, 0.0),
+                                   (0.1, 0.0, 5, 0.0), (0.1, 1.0, -1, 0.0),
+                                   (0.1, 1.0, 5, math.nan)]:
+        assert f(P, 4, P, P, 4, 4, reg, reg_m, iters, tol, P, 1 << 20, ctypes.byref(o), None,
+                 None) == uot.UOT_ERR_INVALID_ARG
+    # workspace too small / misaligned
+    assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 16, ctypes.byref(o), None,
+             None) == uot.UOT_ERR_WORKSPACE
+    assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, ctypes.c_void_p(4096 + 8), 1 << 20,
+             ctypes.byref(o), None, None) == uot.UOT_ERR_WORKSPACE
+    # bad dtype, nonzero reserved, cluster out of range
+    for field, val in [("dtype", 7), ("cluster", 9), ("algo", 3)]:
+        bad = uot.options()
+        setattr(bad, field, val)
+        assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 1 << 20, ctypes.byref(bad), None,
+                 None) == uot.UOT_ERR_INVALID_ARG
+    bad = uot.options()
+    bad.reserved[1] = 1
+    assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 1 << 20, ctypes.byref(bad), None,
+             None) == uot.UOT_ERR_INVALID_ARG
+    g = lib.uot_init_kernel
+    assert g(None, 4, P, 4, 4, 4, 0.1, None, None) == uot.UOT_ERR_INVALID_ARG
+    assert g(P, 4, P, 4, 4, 4, -1.0, None, None) == uot.UOT_ERR_INVALID_ARG
+    h = lib.uot_cost
+    assert h(P, 4, P, 4, 4, 4, 0, None, None) == uot.UOT_ERR_INVALID_ARG
+    assert h(P, 2, P, 4, 4, 4, 0, P, None) == uot.UOT_ERR_INVALID_ARG
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_2412_11079_gb300 import uot
+    saved = uot._lib
+    uot._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="libuot.so not found"):
+            uot.load(str(tmp_path / "missing.so"))
+    finally:
+        uot._lib = saved
+
+
+def test_product_path_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2412_11079_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f
+                assert "oracle/" not in text, f
