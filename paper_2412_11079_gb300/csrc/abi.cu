@@ -150,7 +150,7 @@ uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b,
     if (fused_geometry(k, cs, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
   }
 
-  if (launch_reset(ws, L, s) != cudaSuccess) return UOT_ERR_CUDA;
+  if (launch_reset(ws, L, b, M, s) != cudaSuccess) return UOT_ERR_CUDA;
   cudaEvent_t ev0 = static_cast<cudaEvent_t>(o.pass_events[0]);
   cudaEvent_t ev1 = static_cast<cudaEvent_t>(o.pass_events[1]);
   if (ev0 && cudaEventRecord(ev0, s) != cudaSuccess) return UOT_ERR_CUDA;
@@ -182,6 +182,11 @@ uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b,
     A.r_prev = reinterpret_cast<float*>(ws + L.r);
     A.ctl = reinterpret_cast<Control*>(ws + L.ctl);
     A.stages = stages;
+    A.b_ws = reinterpret_cast<const float*>(ws + L.bws);
+    A.dynamic = 1;
+    A.beta = reinterpret_cast<const float*>(ws + L.beta);
+    A.beta_out = reinterpret_cast<float*>(ws + L.beta);
+    int* ctr = reinterpret_cast<int*>(ws + L.ctr);
     float* c[3];
     double* er[3];
     for (int q = 0; q < 3; ++q) {
@@ -198,11 +203,15 @@ uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b,
       A.err_prev = er[(t - 1) % 3];
       A.err_next = er[t % 3];
       A.err_clear = er[(t + 1) % 3];
+      A.row_ctr = ctr + t % 3;
+      A.ctr_clear = ctr + (t + 1) % 3;
+      A.arrive = ctr + 3 + t % 3;
+      A.arrive_clear = ctr + 3 + (t + 1) % 3;
       if (fused_launch(k, cs, grid, smem, tma, A, s) != cudaSuccess) return UOT_ERR_CUDA;
     }
     if (ev1 && cudaEventRecord(ev1, s) != cudaSuccess) return UOT_ERR_CUDA;
-    if (launch_finish(plan, ldp, N, M, o.dtype, b, fi, iters, ws, L, tol, o.check_every, s) !=
-        cudaSuccess)
+    if (launch_finish(plan, ldp, N, M, o.dtype, b, fi, iters, ws, L, tol, o.check_every, true,
+                      s) != cudaSuccess)
       return UOT_ERR_CUDA;
   }
   if (!out) return UOT_OK;

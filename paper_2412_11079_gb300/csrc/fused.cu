@@ -20,12 +20,23 @@
 // per row (a plain CTA barrier when cs == 1).  The scaled row goes back with
 // 16-byte streaming stores, and each CTA folds its column partials into the
 // global column sums once, at the end of the pass, with vector reductions
-// (red.global.add.v4.f32).  Clusters are persistent over rows: cluster g
-// takes rows g, g + G, g + 2G, ...
+// (red.global.add.v4.f32).
+//
+// Rows are scheduled dynamically when a row fits one CTA: CTAs take rows
+// from a per-pass counter (the next index fetched one step ahead), so SMs
+// that stream faster take more rows and the pass ends within about one row
+// time on every SM; the direction alternates between passes so a pass starts
+// on rows the previous pass wrote last.  The next pass's column factors are
+// computed once: the last 16 CTAs to finish a pass each take 1/16 of the
+// columns after all column partials have landed.  Clusters (rows wider than
+// one CTA) and the path without bulk copies keep a static schedule: cluster
+// g takes rows g, g + G, g + 2G, ...
 //
 // Column partial sums are combined with floating-point atomics, so their
 // order (and the last bits of the column sums) can differ from run to run.
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "uot_device.cuh"
 #include "uot_internal.h"
@@ -35,6 +46,7 @@ namespace uot {
 namespace {
 
 constexpr int MAX_CLUSTER = 8;
+constexpr int BETA_CTAS = 16;  // CTAs that compute the next column factors
 
 template <typename T, int THREADS, int KV, bool TMA>
 __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs p) {
@@ -80,28 +92,109 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
     }
   }
 
-  // Pending column factors of this thread's columns.
   const int m = p.m;
+  const int n = p.n;
   const int col0 = int(cr) * W;
+  const int valid = max(0, min(W, m - col0));
+  const uint32_t copy_bytes = uint32_t((size_t(valid) * sizeof(T)) & ~size_t(15));
+  T* plan = reinterpret_cast<T*>(p.plan);
+  const int64_t ldp = p.ldp;
   uint32_t st = 0;
+
+  // Row schedule.  Dynamic (one CTA per row, bulk-copy path): CTAs take rows
+  // from this pass's counter, so CTAs that stream faster take more rows and
+  // all finish within about one row of each other.  Static (clusters, or the
+  // path without bulk copies): cluster g takes rows g, g + G, g + 2G, ...
+  const bool dyn = TMA && p.dynamic && cs == 1;
+  const int nq = cid < n ? (n - 1 - cid) / ncl + 1 : 0;  // static rows
+  int* slot_row = reinterpret_cast<int*>(bars + (TMA ? stages : 1));
+  uint64_t policy = 0;
+  int issued = 0;     // steps whose slot has been armed (thread 0 only)
+  int next_row = n;   // dynamic: row index fetched one step ahead (thread 0)
+
+  if constexpr (TMA) {
+    // Evict-first loads and streaming stores measured fastest (evict-normal
+    // loads/stores and evict-last stores for the rows the next pass reads
+    // first were slower).
+    policy = policy_evict_first();
+    if (tid == 0) {
+      for (int s2 = 0; s2 < stages; ++s2) mbar_init(&bars[s2], 1);
+      fence_mbar_init();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+  }
+  // All CTAs of the cluster must be running before distributed shared memory
+  // is written; the same barrier publishes the mbarrier initialisation.
+  if (cs > 1) cluster_sync(); else __syncthreads();
+
+  // Arms the slot of step q with `row` (row < 0 or >= n: end of the rows).
+  // Dynamic rows alternate direction from pass to pass, so a pass starts on
+  // the rows the previous pass wrote last, which are still in L2.
+  const bool flip = dyn && (p.t & 1) == 0;
+  auto arm = [&](int q, int row) {
+    if constexpr (TMA) {
+      const int slot = q % stages;
+      if (row >= 0 && row < n) {
+        if (flip) row = n - 1 - row;
+        slot_row[slot] = row;
+        if (copy_bytes) {
+          mbar_arrive_expect_tx(&bars[slot], copy_bytes);
+          bulk_load(ring + size_t(slot) * ROW_BYTES, plan + int64_t(row) * ldp + col0,
+                    copy_bytes, &bars[slot], policy);
+        } else {
+          mbar_arrive(&bars[slot]);
+        }
+      } else {
+        slot_row[slot] = -1;
+        mbar_arrive(&bars[slot]);
+      }
+    }
+  };
+  if constexpr (TMA) {
+    if (tid == 0) {
+      if (dyn) {
+        const int base = atomicAdd(p.row_ctr, stages);
+        for (int q = 0; q < stages; ++q) arm(q, base + q);
+        issued = stages;
+        if (base + stages < n) next_row = atomicAdd(p.row_ctr, 1);
+      } else {
+        const int first = min(stages, nq);
+        for (int q = 0; q < first; ++q) arm(q, cid + q * ncl);
+        issued = first;
+      }
+    }
+  }
+
+  // Pending column factors of this thread's columns: beta_{t-1} was computed
+  // once, at the end of the previous pass, by that pass's last CTAs.
   float beta[KV][VE];
 #pragma unroll
   for (int k = 0; k < KV; ++k) {
     const int cc = col0 + (k * THREADS + tid) * VE;
+    if (p.first) {
 #pragma unroll
-    for (int e = 0; e < VE; ++e) {
-      const int j = cc + e;
-      float bj = 0.0f;
-      if (j < m) bj = p.first ? 1.0f : rescale_factor(__ldg(p.b + j), p.c_prev[j], p.fi, st);
-      beta[k][e] = bj;
+      for (int e = 0; e < VE; ++e) beta[k][e] = (cc + e < m) ? 1.0f : 0.0f;
+    } else if (cc < m) {  // the factor buffer is zero-padded to a multiple of 64
+#pragma unroll
+      for (int e = 0; e < VE; e += 4) {
+        const float4 b4 = __ldcg(reinterpret_cast<const float4*>(p.beta + cc + e));
+        beta[k][e] = b4.x; beta[k][e + 1] = b4.y; beta[k][e + 2] = b4.z; beta[k][e + 3] = b4.w;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < VE; ++e) beta[k][e] = 0.0f;
     }
   }
 
-  // Clear the column-sum (and stopping-error) buffers of iteration t+1.
+  // Clear the column-sum, row-counter and stopping-error buffers of t+1.
   {
     const int g = blockIdx.x * THREADS + tid;
     const int gs = gridDim.x * THREADS;
     for (int j = g; j < p.mpad; j += gs) p.c_clear[j] = 0.0f;
+    if (blockIdx.x == 0 && tid == 0) {
+      *p.ctr_clear = 0;
+      *p.arrive_clear = 0;
+    }
     if (p.track && blockIdx.x == 0 && tid < 2) p.err_clear[tid] = 0.0;
   }
 
@@ -111,58 +204,23 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
 #pragma unroll
     for (int e = 0; e < VE; ++e) cacc[k][e] = 0.0f;
 
-  const int n = p.n;
-  const int nq = cid < n ? (n - 1 - cid) / ncl + 1 : 0;
-  const int valid = max(0, min(W, m - col0));
-  const uint32_t copy_bytes = uint32_t((size_t(valid) * sizeof(T)) & ~size_t(15));
-  T* plan = reinterpret_cast<T*>(p.plan);
-  const int64_t ldp = p.ldp;
-  uint64_t policy = 0;
-  int issued = 0;  // copies issued (thread 0 only)
-
-  if (TMA) {
-    policy = policy_evict_first();
-    if (tid == 0) {
-      for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
-      fence_mbar_init();
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-  }
-  // All CTAs of the cluster must be running before distributed shared memory
-  // is written; the same barrier publishes the mbarrier initialisation.
-  if (cs > 1) cluster_sync(); else __syncthreads();
-
-  auto issue = [&](int q) {
-    const int row = cid + q * ncl;
-    const int slot = q % stages;
-    if (copy_bytes) {
-      mbar_arrive_expect_tx(&bars[slot], copy_bytes);
-      bulk_load(ring + size_t(slot) * ROW_BYTES, plan + int64_t(row) * ldp + col0, copy_bytes,
-                &bars[slot], policy);
-    } else {
-      mbar_arrive(&bars[slot]);
-    }
-  };
-  if (TMA && tid == 0) {
-    const int first = min(stages, nq);
-    for (int q = 0; q < first; ++q) issue(q);
-    issued = first;
-  }
-
   bool broken = false;
+  int done_rows = 0;
   double err_num = 0.0, err_den = 0.0;
 
-  for (int q = 0; q < nq; ++q) {
-    const int row = cid + q * ncl;
-    const float arow = __ldg(p.a + row);
-    T* grow = plan + int64_t(row) * ldp;
+  for (int q = 0;; ++q) {
+    int row;
     float x[KV][VE];
-    if (TMA) {
+    if constexpr (TMA) {
+      if (!dyn && q >= nq) break;
       const int slot = q % stages;
       if (!broken && !mbar_wait_bounded(&bars[slot], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS)) {
         broken = true;
         st |= DEV_TIMEOUT;
       }
+      row = *reinterpret_cast<volatile int*>(&slot_row[slot]);
+      if (row < 0 || row >= n) break;  // uniform: every thread reads the same slot
+      const T* grow = plan + int64_t(row) * ldp;
       const unsigned char* srow = ring + size_t(slot) * ROW_BYTES;
 #pragma unroll
       for (int k = 0; k < KV; ++k) {
@@ -176,6 +234,9 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
         }
       }
     } else {
+      if (q >= nq) break;
+      row = cid + q * ncl;
+      const T* grow = plan + int64_t(row) * ldp;
 #pragma unroll
       for (int k = 0; k < KV; ++k) {
         const int cc = col0 + (k * THREADS + tid) * VE;
@@ -183,6 +244,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
         for (int e = 0; e < VE; ++e) x[k][e] = (cc + e < m) ? E::load1(grow + cc + e) : 0.0f;
       }
     }
+    const float arow = __ldg(p.a + row);
+    T* grow = plan + int64_t(row) * ldp;
 
     // Column step of iteration t-1 on this row, then its sum.
     float s = 0.0f;
@@ -202,11 +265,30 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
         for (uint32_t r = 0; r < cs; ++r) st_cluster_f32(map_shared_rank(rb + cr * NW + warp, r), s);
       }
     }
-    if (cs > 1) cluster_sync(); else __syncthreads();
-    // Every thread has finished reading this slot: refill it.
-    if (TMA && tid == 0 && !broken && issued < nq) {
-      issue(issued);
-      ++issued;
+    if (cs > 1) {
+      cluster_sync();  // static rows: the loop is bounded by nq
+    } else if (__syncthreads_or(broken ? 1 : 0)) {
+      // A copy never completed: leave together (the data of this step is not
+      // valid); copies still in flight are waited for below.
+      broken = true;
+      st |= DEV_TIMEOUT;
+      break;
+    }
+    // Every thread has finished reading this slot: re-arm it.
+    if constexpr (TMA) {
+      if (tid == 0 && !broken) {
+        if (dyn) {
+          const int r2 = next_row;
+          arm(issued, r2);
+          ++issued;
+          if (r2 < n) {
+            next_row = atomicAdd(p.row_ctr, 1);
+          }
+        } else if (issued < nq) {
+          arm(issued, cid + issued * ncl);
+          ++issued;
+        }
+      }
     }
     float tot = 0.0f;
     for (uint32_t r = 0; r < cs; ++r)
@@ -238,10 +320,11 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
       err_den += d;
       p.r_prev[row] = tot;
     }
+    ++done_rows;
   }
 
   // Fold this CTA's column partials into the column sums of iteration t.
-  if (nq > 0) {
+  if (done_rows > 0) {
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
       const int cc = col0 + (k * THREADS + tid) * VE;
@@ -256,17 +339,52 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
       }
     }
   }
-  if (p.track && cr == 0 && tid == 0 && nq > 0) {
+  if (p.track && cr == 0 && tid == 0 && done_rows > 0) {
     atomicAdd(&p.err_next[0], err_num);
     atomicAdd(&p.err_next[1], err_den);
   }
   if (st) atomicOr(&ctl->status, st);
 
+  // beta_t = (b_j / c_j)^fi for the next pass, computed once: the last K CTAs
+  // to finish this pass each take 1/K of the columns, after waiting (bounded)
+  // for every CTA's column partials to land.  Only CTAs already running are
+  // waited for, so this needs no co-residency guarantee.
+  __syncthreads();
+  __shared__ int s_arrival;
+  if (tid == 0) {
+    __threadfence();
+    s_arrival = atomicAdd(p.arrive, 1);
+  }
+  __syncthreads();
+  const int G = int(gridDim.x);
+  const int K = min(G, BETA_CTAS);
+  const int slice = s_arrival - (G - K);
+  if (slice >= 0) {
+    if (tid == 0) {
+      const uint64_t t0 = global_timer_ns();
+      while (ld_acquire_gpu(p.arrive) < G) {
+        if (global_timer_ns() - t0 > WAIT_LIMIT_NS) {
+          atomicOr(&ctl->status, DEV_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    const int per = (m + K - 1) / K;
+    const int j0 = slice * per, j1 = min(m, j0 + per);
+    uint32_t st2 = 0;
+    for (int j = j0 + tid; j < j1; j += THREADS)
+      p.beta_out[j] = rescale_factor(__ldg(p.b_ws + j), __ldcg(p.c_next + j), p.fi, st2);
+    if (st2) atomicOr(&ctl->status, st2);
+  }
+
   // After a timed-out wait, give copies still in flight a bounded chance to
   // land before the CTA (and its shared memory) goes away.
-  if (TMA && tid == 0 && broken) {
-    for (int q = max(0, issued - stages); q < issued; ++q)
-      mbar_wait_bounded(&bars[q % stages], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS);
+  if constexpr (TMA) {
+    if (tid == 0 && broken) {
+      for (int q = max(0, issued - stages); q < issued; ++q)
+        mbar_wait_bounded(&bars[q % stages], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS);
+    }
   }
 }
 
@@ -303,7 +421,49 @@ size_t elem_size(int dtype) { return dtype == UOT_F32 ? 4 : 2; }
 size_t smem_bytes(const FusedConfig& c, int stages) {
   const size_t row = size_t(c.cols) * elem_size(c.dtype);
   const size_t red = 2 * MAX_CLUSTER * (c.threads / 32) * sizeof(float);
-  return size_t(stages) * row + red + size_t(stages > 0 ? stages : 1) * 8;
+  const size_t slots = size_t(stages > 0 ? stages : 1);
+  return size_t(stages) * row + red + slots * 8 + slots * 4;
+}
+
+// cudaFuncSetAttribute is a host call that can wait for running work on the
+// device; re-issuing it before every iteration pass kept the host in lockstep
+// with the GPU.  Attributes are therefore set once per (device, kernel) and
+// the launch geometry is cached per (device, config, cluster, rows).
+constexpr int MAX_DEV = 64;
+std::mutex g_mu;
+size_t g_smem_set[MAX_DEV][kNum][2];
+bool g_cluster_set[MAX_DEV][kNum][2];
+
+struct GeoKey {
+  int dev, k, cs, n;
+  bool operator==(const GeoKey& o) const {
+    return dev == o.dev && k == o.k && cs == o.cs && n == o.n;
+  }
+};
+struct GeoVal {
+  int grid, stages;
+  size_t smem;
+};
+constexpr int GEO_CACHE = 64;
+GeoKey g_geo_key[GEO_CACHE];
+GeoVal g_geo_val[GEO_CACHE];
+int g_geo_used = 0, g_geo_next = 0;
+
+cudaError_t ensure_attributes(int dev, int k, bool tma, size_t smem, bool cluster) {
+  if (dev < 0 || dev >= MAX_DEV) return cudaErrorInvalidDevice;
+  const void* fn = tma ? kTable[k].fn_tma : kTable[k].fn_plain;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (g_smem_set[dev][k][tma] < smem) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    g_smem_set[dev][k][tma] = smem;
+  }
+  if (cluster && !g_cluster_set[dev][k][tma]) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    g_cluster_set[dev][k][tma] = true;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -339,6 +499,17 @@ cudaError_t fused_geometry(int k, int cs, int n, int* grid, int* stages, size_t*
   int dev = 0, sms = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
+  const GeoKey key{dev, k, cs, n};
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    for (int i = 0; i < g_geo_used; ++i)
+      if (g_geo_key[i] == key) {
+        *grid = g_geo_val[i].grid;
+        *stages = g_geo_val[i].stages;
+        *smem = g_geo_val[i].smem;
+        return cudaSuccess;
+      }
+  }
   err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (err != cudaSuccess) return err;
   int optin = 0;
@@ -388,6 +559,14 @@ cudaError_t fused_geometry(int k, int cs, int n, int* grid, int* stages, size_t*
   const int cap = (n + 1) / 2;
   if (clusters > cap) clusters = cap > 0 ? cap : 1;
   *grid = clusters * cs;
+  err = ensure_attributes(dev, k, false, smem_bytes(e.cfg, 0), cs > 1);
+  if (err != cudaSuccess) return err;
+  err = ensure_attributes(dev, k, true, *smem, cs > 1);
+  if (err != cudaSuccess) return err;
+  std::lock_guard<std::mutex> lock(g_mu);
+  const int slot = g_geo_used < GEO_CACHE ? g_geo_used++ : (g_geo_next++ % GEO_CACHE);
+  g_geo_key[slot] = key;
+  g_geo_val[slot] = GeoVal{*grid, *stages, *smem};
   return cudaSuccess;
 }
 
@@ -396,12 +575,6 @@ cudaError_t fused_launch(int k, int cs, int grid, size_t smem, bool tma, const F
   const Entry& e = kTable[k];
   const void* fn = tma ? e.fn_tma : e.fn_plain;
   size_t bytes = tma ? smem : smem_bytes(e.cfg, 0);
-  cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-  if (err != cudaSuccess) return err;
-  if (cs > 1) {
-    err = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (err != cudaSuccess) return err;
-  }
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -416,7 +589,7 @@ cudaError_t fused_launch(int k, int cs, int grid, size_t smem, bool tma, const F
   cfg.numAttrs = cs > 1 ? 1 : 0;
   FusedArgs a = args;
   void* kargs[] = {&a};
-  err = cudaLaunchKernelExC(&cfg, fn, kargs);
+  cudaError_t err = cudaLaunchKernelExC(&cfg, fn, kargs);
   if (err == cudaSuccess) count_launch();
   return err;
 }

@@ -14,6 +14,18 @@ namespace {
 
 constexpr int TB = 256;
 
+// exp(-c/reg) without the error of rounding the exponent to FP32 first: with
+// hi = fl(-c/reg), the residual -c - hi*reg is exact in FP32 (it is the
+// remainder of a correctly rounded division), so -c/reg = hi + e/reg and
+// exp(-c/reg) = expf(hi) * exp(e/reg), where |e/reg| <= |hi| 2^-24 lets the
+// second factor be taken to first order.
+__device__ __forceinline__ float gibbs(float c, float reg) {
+  const float hi = -c / reg;
+  const float e = fmaf(-hi, reg, -c);
+  const float x = expf(hi);
+  return fmaf(x, e / reg, x);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TB) init_kernel(const float* __restrict__ C, int64_t ldc,
                                                   T* __restrict__ P, int64_t ldp, int n, int m,
@@ -22,7 +34,7 @@ __global__ void __launch_bounds__(TB) init_kernel(const float* __restrict__ C, i
   if (j >= m) return;
   for (int i = blockIdx.y; i < n; i += gridDim.y) {
     const float c = C[int64_t(i) * ldc + j];
-    Elem<T>::store1(P + int64_t(i) * ldp + j, expf(-c / reg));
+    Elem<T>::store1(P + int64_t(i) * ldp + j, gibbs(c, reg));
   }
 }
 
@@ -33,7 +45,8 @@ __global__ void __launch_bounds__(TB) finish_kernel(T* __restrict__ P, int64_t l
                                                     const float* __restrict__ b, float fi,
                                                     int iters, const float* c0, const float* c1,
                                                     const float* c2, const double* err_ring,
-                                                    Control* ctl, double tol, int check_every) {
+                                                    Control* ctl, double tol, int check_every,
+                                                    const float* beta_ready) {
   const int done = ctl->done;
   const int t = done ? ctl->stop_iter : iters;
   const float* c = (t % 3 == 0) ? c0 : (t % 3 == 1) ? c1 : c2;
@@ -47,7 +60,8 @@ __global__ void __launch_bounds__(TB) finish_kernel(T* __restrict__ P, int64_t l
   const int j = blockIdx.x * TB + threadIdx.x;
   if (j >= m) return;
   uint32_t st = 0;
-  const float beta = rescale_factor(b[j], c[j], fi, st);
+  // The fused passes leave beta_t ready (its status was recorded there).
+  const float beta = beta_ready ? beta_ready[j] : rescale_factor(b[j], c[j], fi, st);
   if (st && blockIdx.y == 0) atomicOr(&ctl->status, st);
   for (int i = blockIdx.y; i < n; i += gridDim.y) {
     T* q = P + int64_t(i) * ldp + j;
@@ -75,7 +89,8 @@ __global__ void __launch_bounds__(TB) cost_kernel(const T* __restrict__ P, int64
   }
 }
 
-__global__ void reset_kernel(Control* ctl, double* err_ring, float* c1, int mpad) {
+__global__ void reset_kernel(Control* ctl, double* err_ring, float* c1, int mpad, const float* b,
+                             float* b_ws, int m, int* ctr, float* beta) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g == 0) {
     ctl->status = 0;
@@ -85,7 +100,12 @@ __global__ void reset_kernel(Control* ctl, double* err_ring, float* c1, int mpad
     ctl->err = __longlong_as_double(0x7ff0000000000000ll);
   }
   if (g < 6) err_ring[g] = 0.0;
-  for (int j = g; j < mpad; j += gridDim.x * blockDim.x) c1[j] = 0.0f;
+  if (g < 6) ctr[g] = 0;
+  for (int j = g; j < mpad; j += gridDim.x * blockDim.x) {
+    c1[j] = 0.0f;
+    b_ws[j] = j < m ? b[j] : 0.0f;
+    beta[j] = 0.0f;
+  }
 }
 
 // ---- multi-pass iteration: 5 launches, 3 reads + 2 writes of the plan ----
@@ -206,7 +226,7 @@ cudaError_t launch_init(const float* C, int64_t ldc, void* P, int64_t ldp, int n
 
 cudaError_t launch_finish(void* P, int64_t ldp, int n, int m, int dtype, const float* b, float fi,
                           int iters, const uint8_t* ws, WsLayout L, double tol, int check_every,
-                          cudaStream_t s) {
+                          bool beta_ready, cudaStream_t s) {
   uint8_t* w = const_cast<uint8_t*>(ws);
   return by_dtype(dtype, [&](auto z) {
     using T = decltype(z);
@@ -214,7 +234,7 @@ cudaError_t launch_finish(void* P, int64_t ldp, int n, int m, int dtype, const f
         reinterpret_cast<T*>(P), ldp, n, m, b, fi, iters, reinterpret_cast<const float*>(w + L.c[0]),
         reinterpret_cast<const float*>(w + L.c[1]), reinterpret_cast<const float*>(w + L.c[2]),
         reinterpret_cast<const double*>(w + L.err), reinterpret_cast<Control*>(w + L.ctl), tol,
-        check_every);
+        check_every, beta_ready ? reinterpret_cast<const float*>(w + L.beta) : nullptr);
     return last();
   });
 }
@@ -231,11 +251,14 @@ cudaError_t launch_cost(const void* P, int64_t ldp, const float* C, int64_t ldc,
   });
 }
 
-cudaError_t launch_reset(uint8_t* ws, WsLayout L, cudaStream_t s) {
+cudaError_t launch_reset(uint8_t* ws, WsLayout L, const float* b, int m, cudaStream_t s) {
   const int blocks = int((L.mpad + TB - 1) / TB);
   reset_kernel<<<blocks, TB, 0, s>>>(reinterpret_cast<Control*>(ws + L.ctl),
                                      reinterpret_cast<double*>(ws + L.err),
-                                     reinterpret_cast<float*>(ws + L.c[1]), int(L.mpad));
+                                     reinterpret_cast<float*>(ws + L.c[1]), int(L.mpad), b,
+                                     reinterpret_cast<float*>(ws + L.bws), m,
+                                     reinterpret_cast<int*>(ws + L.ctr),
+                                     reinterpret_cast<float*>(ws + L.beta));
   return last();
 }
 

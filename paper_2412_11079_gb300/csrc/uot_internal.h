@@ -6,7 +6,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
-#include "../../include/uot.h"
+#include "uot.h"
 
 namespace uot {
 
@@ -35,6 +35,9 @@ struct WsLayout {
   size_t r;       // float[npad]: previous row sums (stopping rule)
   size_t f;       // float[npad]: row factors (multi-pass algorithm)
   size_t g;       // float[mpad]: column factors (multi-pass algorithm)
+  size_t bws;     // float[mpad]: copy of b, zero-padded (aligned vector loads)
+  size_t ctr;     // int32[6]: per-pass row counters and arrival counters, rings of 3
+  size_t beta;    // float[mpad]: column factors of the last completed pass
   size_t total;
   int64_t mpad, npad;
 };
@@ -52,6 +55,9 @@ inline WsLayout ws_layout(int64_t n, int64_t m) {
   L.r = off; off = align256(off + size_t(L.npad) * 4);
   L.f = off; off = align256(off + size_t(L.npad) * 4);
   L.g = off; off = align256(off + size_t(L.mpad) * 4);
+  L.bws = off; off = align256(off + size_t(L.mpad) * 4);
+  L.ctr = off; off = align256(off + 6 * sizeof(int32_t));
+  L.beta = off; off = align256(off + size_t(L.mpad) * 4);
   L.total = off;
   return L;
 }
@@ -79,6 +85,14 @@ struct FusedArgs {
   double* err_clear;
   Control* ctl;
   int stages;          // ring depth
+  const float* b_ws;   // b, zero-padded to mpad (16-byte aligned)
+  int* row_ctr;        // rows taken so far in this pass (dynamic schedule)
+  int* ctr_clear;      // counter to clear for iteration t+1
+  int dynamic;         // 1: dynamic row schedule (single-CTA rows, bulk copies)
+  int* arrive;         // CTAs that finished this pass
+  int* arrive_clear;   // arrival counter to clear for iteration t+1
+  const float* beta;   // beta_{t-1}, zero-padded to mpad (read unless first)
+  float* beta_out;     // beta_t, written by the last CTAs of this pass
 };
 
 struct FusedConfig {
@@ -104,10 +118,10 @@ cudaError_t launch_init(const float* C, int64_t ldc, void* P, int64_t ldp, int n
                         float reg, int dtype, cudaStream_t s);
 cudaError_t launch_finish(void* P, int64_t ldp, int n, int m, int dtype, const float* b,
                           float fi, int iters, const uint8_t* ws, WsLayout L, double tol,
-                          int check_every, cudaStream_t s);
+                          int check_every, bool beta_ready, cudaStream_t s);
 cudaError_t launch_cost(const void* P, int64_t ldp, const float* C, int64_t ldc, int n, int m,
                         int dtype, double* out, cudaStream_t s);
-cudaError_t launch_reset(uint8_t* ws, WsLayout L, cudaStream_t s);
+cudaError_t launch_reset(uint8_t* ws, WsLayout L, const float* b, int m, cudaStream_t s);
 cudaError_t launch_multipass_iter(void* P, int64_t ldp, int n, int m, int dtype, const float* a,
                                   const float* b, float fi, int t, double tol, int check_every,
                                   uint8_t* ws, WsLayout L, cudaStream_t s, int* launches);

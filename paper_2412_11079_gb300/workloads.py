@@ -40,6 +40,12 @@ class Problem:
     iters: int
     name: str = ""
 
+    def __post_init__(self):
+        # The C ABI takes reg and reg_m as FP32: hand both sides the same
+        # FP32-representable values.
+        self.reg = float(np.float32(self.reg))
+        self.reg_m = float(np.float32(self.reg_m))
+
     @property
     def shape(self):
         return self.C.shape

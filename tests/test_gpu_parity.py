@@ -118,14 +118,14 @@ def fused_configs(uot, dtype_code):
 
 @pytest.mark.parametrize("m", [1000, 2999])
 def test_every_fp32_config_and_cluster(uot, m):
-    """Each fused configuration, with every cluster size 1..8 that covers m."""
+    """Each FP32 fused configuration at the smallest cluster size that covers
+    m, and one size larger (its last CTA then owns no columns)."""
     p = workloads.uniform2d(seed=m, n=150, m=m, reg=0.1, reg_m=0.9, iters=10)
     ref, _ = run_oracle(p)
     for k, c in fused_configs(uot, uot.UOT_F32):
-        for cs in range(1, 9):
-            if cs * c["cols"] < m or (cs - 1) * c["cols"] >= m + c["cols"]:
-                continue
-            if cs > 1 and (cs - 1) * c["cols"] >= 4 * m:
+        cs_min = -(-m // c["cols"])
+        for cs in (cs_min, cs_min + 1):
+            if cs > 8:
                 continue
             got, _, res, _ = run_gpu(uot, p, tile=k + 1, cluster=cs)
             assert rel_err(got, ref.plan) <= FP32_TOL, (k, c, cs)
@@ -202,8 +202,9 @@ def test_init_kernel_matches_exp(uot):
     ref = np.exp(-p.C.astype(np.float64) / p.reg)
     got = plan.double().cpu().numpy()
     normal = ref > 1.2e-38
-    # expf and the FP32 division together stay within a few ulp (2^-24).
-    assert np.max(np.abs(got[normal] - ref[normal]) / ref[normal]) < 8e-7
+    # The exponent is carried as hi + residual, so only expf's own error and
+    # the final rounding remain (a few ulp of 2^-24), even where C/reg ~ 95.
+    assert np.max(np.abs(got[normal] - ref[normal]) / ref[normal]) < 6e-7
     assert np.max(np.abs(got[~normal] - ref[~normal])) < 3e-45
 
 
@@ -231,8 +232,12 @@ def test_cost_kernel(uot):
 @pytest.mark.parametrize("dtype,u", [("bfloat16", 2.0 ** -8), ("float16", 2.0 ** -11)])
 @pytest.mark.parametrize("n,m", [(129, 1000), (64, 16385)])
 def test_inplace_16bit_within_rounding_bound(uot, dtype, u, n, m):
+    # Masses n*m and 1.5*n*m keep plan entries O(1), inside FP16's normal
+    # range (entries near 1e-6 would be FP16 subnormals with a few bits).
     T = 4
     p = workloads.uniform2d(seed=18 + m, n=n, m=m, reg=0.5, reg_m=1.0, iters=T)
+    p.a = (p.a * np.float32(n * m)).astype(np.float32)
+    p.b = (p.b * np.float32(n * m)).astype(np.float32)
     got, cost, res, _ = run_gpu(uot, p, dtype=getattr(torch, dtype))
     ref, ref_cost = run_oracle(p)
     bound = 1.25 * (2 * T + 1) * u + 1e-5
