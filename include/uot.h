@@ -158,6 +158,41 @@ uot_status uot_read_result(const void* workspace, int64_t n, int64_t m,
 uot_status uot_cost(const void* plan, int64_t ldp, const float* C, int64_t ldc,
                     int64_t n, int64_t m, int32_t dtype, double* out_dev, void* stream);
 
+/*
+ * uot_sinkhorn_noalloc -- uot_sinkhorn for callers that cannot allocate.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot hand the library a device buffer -- for example a plugin inside a
+ * host application that owns all device memory and offers its plugins no
+ * allocation hook, or code on a latency-critical path that must not call
+ * cudaMalloc (which can synchronise the device) and has no pool to draw from.
+ * It runs exactly uot_sinkhorn, but its scratch memory is a fixed array of
+ * UOT_STATIC_SCRATCH_BYTES bytes compiled into the library: every GPU that
+ * loads the library holds that array until the process exits, and the call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ * The caller still passes the plan and targets.
+ *  - Size limit: problems whose uot_workspace_size(n, m, opt) exceeds
+ *    UOT_STATIC_SCRATCH_BYTES (2 MiB) are rejected with UOT_ERR_WORKSPACE
+ *    before anything is enqueued; N = M = 32768 needs about 1 MiB.
+ *  - Set-up: the first call on a device (with that device current) looks up
+ *    the array's device address once; make that first call before any stream
+ *    capture on that device.
+ *  - Sharing: every call on a device uses the same array, and the array keeps
+ *    the last call's contents (each call re-initialises what must start at
+ *    zero).  Calls whose work overlaps on the GPU -- on different streams, or
+ *    from different host threads -- race on the array and must be serialised
+ *    by the caller.
+ *  - Result: the iteration count, last error and device status live in the
+ *    shared array, so pass `out` (the call then synchronises `stream`) to get
+ *    them; with out == NULL the call is asynchronous and they are not
+ *    retrievable.
+ * Arguments and errors are those of uot_sinkhorn without the workspace.
+ */
+#define UOT_STATIC_SCRATCH_BYTES ((size_t)2 << 20)
+uot_status uot_sinkhorn_noalloc(void* plan, int64_t ldp, const float* a, const float* b,
+                                int64_t n, int64_t m, float reg, float reg_m, int32_t iters,
+                                double tol, const uot_options* opt, void* stream,
+                                uot_result* out);
+
 /* Description of fused-pass configuration k (0-based), for tuning tools:
  * writes dtype, threads per CTA, 16-byte vectors per thread per row and the
  * columns one CTA covers.  Returns the number of configurations when k < 0 or

@@ -65,6 +65,9 @@ SIGNATURES = {
     "uot_read_result": (ctypes.c_int, [_P, _I64, _I64, ctypes.POINTER(UotOptions), _P,
                                        ctypes.POINTER(UotResult)]),
     "uot_cost": (ctypes.c_int, [_P, _I64, _P, _I64, _I64, _I64, _I32, _P, _P]),
+    "uot_sinkhorn_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _D,
+                                            ctypes.POINTER(UotOptions), _P,
+                                            ctypes.POINTER(UotResult)]),
     "uot_fused_config": (_I32, [_I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                 ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
 }
@@ -214,6 +217,29 @@ def uot_sinkhorn(plan, a, b, reg: float, reg_m: float, iters: int, tol: float = 
     if st not in (UOT_OK, UOT_ERR_NONFINITE, UOT_ERR_ZERO_SUM, UOT_ERR_TIMEOUT) or (
             check_status and st != UOT_OK):
         raise UotError(st, "uot_sinkhorn")
+    return SinkhornResult(res.iters_done, res.dev_status, res.err)
+
+
+UOT_STATIC_SCRATCH_BYTES = 2 << 20
+
+
+def uot_sinkhorn_noalloc(plan, a, b, reg: float, reg_m: float, iters: int, tol: float = 0.0,
+                         opt: UotOptions | None = None, stream=None,
+                         check_status: bool = True):
+    """uot_sinkhorn on the library's built-in scratch array (no workspace, no
+    device allocation); synchronous, returns a SinkhornResult."""
+    n, m = plan.shape
+    opt = opt or options(dtype_code(plan.dtype))
+    if opt.dtype != dtype_code(plan.dtype):
+        raise ValueError("options dtype does not match the plan tensor")
+    pp, ldp = _matrix(plan, "plan")
+    res = UotResult()
+    st = load().uot_sinkhorn_noalloc(pp, ldp, _vector(a, "a", n), _vector(b, "b", m), n, m,
+                                     float(reg), float(reg_m), int(iters), float(tol),
+                                     ctypes.byref(opt), _stream(stream), ctypes.byref(res))
+    if st not in (UOT_OK, UOT_ERR_NONFINITE, UOT_ERR_ZERO_SUM, UOT_ERR_TIMEOUT) or (
+            check_status and st != UOT_OK):
+        raise UotError(st, "uot_sinkhorn_noalloc")
     return SinkhornResult(res.iters_done, res.dev_status, res.err)
 
 
