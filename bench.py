@@ -161,6 +161,87 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def run_precision(args):
+    """Reduced-precision workload: N=M=32768 (2-D uniform points, reg 0.1,
+    reg_m 1.0, 300 iterations) timed for every storage form, and the error
+    of each form against the FP64 oracle on the 8192^2 instance."""
+    import torch
+
+    import oracle
+    from paper_2412_11079_gb300 import build, uot, workloads
+
+    build.build()
+    uot.load()
+    dev = torch.device("cuda", 0)
+    n = m = args.n
+    iters = args.iters
+    C, a, b, reg, reg_m, _ = workloads.uniform2d_device(0, n, m, dev, 0.1, 1.0, iters)
+    forms = [("f32", "inplace", torch.float32, 0), ("f32", "kform", torch.float32, 0),
+             ("bf16", "kform", torch.bfloat16, 0), ("f16", "kform", torch.float16, 15),
+             ("bf16", "inplace", torch.bfloat16, 0), ("f16", "inplace", torch.float16, 0)]
+    out = {}
+    for name, form, dt, scale in forms:
+        mat = torch.empty((n, m), dtype=dt, device=dev)
+        opt = uot.options(uot.dtype_code(dt))
+        ws = uot.workspace(n, m, opt, dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(); e1.record()
+        opt.pass_events[0] = e0.cuda_event
+        opt.pass_events[1] = e1.cuda_event
+        U = torch.empty(n, device=dev)
+        V = torch.empty(m, device=dev)
+        times = []
+        for rep in range(1 + args.steps):
+            if form == "kform":
+                uot.uot_init_kernel_scaled(C, mat, reg, scale, opt)
+                uot.uot_sinkhorn_kform(mat, a, b, reg, reg_m, iters, 0.0, scale, U, V, ws, opt)
+            else:
+                uot.uot_init_kernel(C, mat, reg, opt)
+                uot.uot_sinkhorn(plan=mat, a=a, b=b, reg=reg, reg_m=reg_m, iters=iters, ws=ws,
+                                 opt=opt, check_status=False)
+            torch.cuda.synchronize()
+            if rep:
+                times.append(e0.elapsed_time(e1) / iters)
+        t = min(times)
+        bytes_per = (2 if form == "inplace" else 1) * mat.element_size()
+        out[f"{name}_{form}"] = {"ms_per_iter": t, "elems_per_s": n * m / (t * 1e-3),
+                                 "alg_gbs": bytes_per * n * m / (t * 1e-3) / 1e9}
+        del mat, ws
+        torch.cuda.empty_cache()
+    del C
+    # Accuracy on the 8192^2 instance against the FP64 oracle.
+    q = workloads.precision_case(seed=0, n=args.acc_n, m=args.acc_n, iters=iters)
+    ref = oracle.sinkhorn(oracle.init_plan(q.C, q.reg), q.a, q.b, q.reg, q.reg_m, q.iters).plan
+    ref_cost = oracle.transport_cost(ref, q.C)
+    floor = 1e-6 * np.abs(ref).max()
+    Cq = torch.from_numpy(q.C).to(dev)
+    aq = torch.from_numpy(q.a).to(dev)
+    bq = torch.from_numpy(q.b).to(dev)
+    for name, form, dt, scale in forms:
+        mat = torch.empty(q.C.shape, dtype=dt, device=dev)
+        opt = uot.options(uot.dtype_code(dt))
+        if form == "kform":
+            uot.uot_init_kernel_scaled(Cq, mat, q.reg, scale, opt)
+            U, V, _ = uot.uot_sinkhorn_kform(mat, aq, bq, q.reg, q.reg_m, iters, 0.0, scale, opt=opt)
+            plan = uot.uot_kform_plan(mat, U, V)
+            cost = uot.uot_kform_cost(mat, U, V, Cq).item()
+        else:
+            uot.uot_init_kernel(Cq, mat, q.reg, opt)
+            uot.uot_sinkhorn(mat, aq, bq, q.reg, q.reg_m, iters, opt=opt, check_status=False)
+            plan = mat
+            cost = uot.uot_cost(mat, Cq).item()
+        got = plan.double().cpu().numpy()
+        out[f"{name}_{form}"].update({
+            "plan_max_rel_err_8192": float(np.max(np.abs(got - ref) / np.maximum(np.abs(ref), floor))),
+            "cost_rel_err_8192": abs(cost - ref_cost) / abs(ref_cost)})
+    base = out["f32_inplace"]["elems_per_s"]
+    for v in out.values():
+        v["speedup_vs_f32_inplace"] = v["elems_per_s"] / base
+    print(json.dumps({"workload": f"precision N=M={n}, 2-D uniform points, reg 0.1, reg_m 1.0, "
+                                  f"{iters} iterations; errors vs FP64 oracle at "
+                                  f"{args.acc_n}^2", "unit": UNIT, "forms": out}), flush=True)
+
+
 def config_of(args):
     return {"workload": f"single UOT problem N=M={args.n}" if args.n == args.m else
             f"single UOT problem {args.n}x{args.m}",
@@ -182,6 +263,8 @@ def main():
     ap.add_argument("--oracle-iters", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--workload", default="large", choices=["large", "precision"])
+    ap.add_argument("--acc-n", type=int, default=8192)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -191,6 +274,13 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "precision":
+        if args.n == 16384 and args.m == 16384:
+            args.n = args.m = 32768
+        if args.iters == 500:
+            args.iters = 300
+        run_precision(args)
         return
 
     import torch
@@ -338,9 +428,28 @@ def main():
         q1.record(stream)
         torch.cuda.synchronize()
         mp_value = float(n) * m * mp_iters * 2 / (q0.elapsed_time(q1) * 1e-3)
+        # BF16 kernel form (read-only K, FP32 scalings) on the same problem.
+        K16 = torch.empty((n, m), dtype=torch.bfloat16, device=dev)
+        ko = uot.options(uot.UOT_BF16)
+        U = torch.empty(n, device=dev)
+        V = torch.empty(m, device=dev)
+        uot.uot_init_kernel_scaled(C, K16, p.reg, 0, ko)
+        uot.uot_sinkhorn_kform(K16, a, b, p.reg, p.reg_m, iters, 0.0, 0, U, V, ws, ko, sync=False)
+        torch.cuda.synchronize()
+        q0.record(stream)
+        for _ in range(2):
+            uot.uot_sinkhorn_kform(K16, a, b, p.reg, p.reg_m, iters, 0.0, 0, U, V, ws, ko,
+                                   sync=False)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        kf_value = float(n) * m * iters * 2 / (q0.elapsed_time(q1) * 1e-3)
+        del K16
         compare = {"plain_fp32_multipass": {"value": mp_value, "unit": UNIT,
                                             "iters": mp_iters},
-                   "fused_over_multipass": value / world / mp_value}
+                   "fused_over_multipass": value / world / mp_value,
+                   "bf16_kernel_form": {"value": kf_value, "unit": UNIT, "iters": iters,
+                                        "alg_gbs": 2.0 * kf_value / 1e9},
+                   "bf16_kform_over_fp32_fused": kf_value / (value / world)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

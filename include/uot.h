@@ -142,6 +142,59 @@ uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b,
                         int32_t iters, double tol, void* workspace, size_t ws_bytes,
                         const uot_options* opt, void* stream, uot_result* out);
 
+/*
+ * Kernel form.  The plan of Section 2.1 is always diag(U) K diag(V), with K
+ * the initial plan and U, V the products of the row and column factors so
+ * far; the same iteration can therefore keep K read-only and update only the
+ * FP32 vectors U (length n) and V (length m).  One fused pass per iteration
+ * (Algorithm 1's single sweep) reads K once -- sizeof(K element) bytes per
+ * element instead of a read and a write of the plan -- and K is rounded only
+ * once, which is what makes 16-bit storage accurate enough.  In real
+ * arithmetic the iterates equal uot_sinkhorn's.
+ *
+ * uot_init_kernel_scaled -- K = exp(-C/reg) * 2^log2_scale in opt->dtype
+ * (log2_scale an integer in [-100, 100]; FP16 needs a positive scale to keep
+ * small entries out of its subnormal range, e.g. 15 when max K = 1).
+ * Errors as uot_init_kernel.
+ */
+uot_status uot_init_kernel_scaled(const float* C, int64_t ldc, void* K, int64_t ldk, int64_t n,
+                                  int64_t m, float reg, float log2_scale,
+                                  const uot_options* opt, void* stream);
+
+/*
+ * uot_sinkhorn_kform -- `iters` iterations of the Section 2.1 rule in kernel
+ * form.  K: n x m of opt->dtype (FP32/BF16/FP16), leading dimension ldk,
+ * read-only, stored scaled by 2^k_log2_scale (integer; 0 if unscaled).  On
+ * return U (n floats) and V (m floats), device arrays owned by the caller,
+ * hold the scalings with the storage scale folded into U, so the plan is
+ * P_ij = U_i K_ij V_j for K as stored.  U and V are determined up to a common
+ * power of two (U 2^e, V 2^-e): at the fixed point the row factors tend to
+ * k = (sum a / sum b)^(fi/(2-fi)) and the column factors to 1/k, so each pass
+ * moves an exact power of two between them to keep both in FP32 range.  U and V are overwritten (the call
+ * starts from U = 2^-k_log2_scale, V = 1).  Row/column sums, factors and
+ * scalings are FP32; the stopping error is FP64 (same rule as uot_sinkhorn).
+ * Only the fused algorithm exists in this form.  Other arguments, the
+ * workspace and errors are those of uot_sinkhorn.
+ */
+uot_status uot_sinkhorn_kform(const void* K, int64_t ldk, const float* a, const float* b,
+                              int64_t n, int64_t m, float reg, float reg_m, int32_t iters,
+                              double tol, float k_log2_scale, float* U, float* V,
+                              void* workspace, size_t ws_bytes, const uot_options* opt,
+                              void* stream, uot_result* out);
+
+/* uot_kform_plan -- materialises P_ij = (U_i K_ij) V_j (FP32 products) into
+ * `plan` (n x m, plan_dtype, leading dimension ldp).  K of k_dtype.  Async. */
+uot_status uot_kform_plan(const void* K, int64_t ldk, int32_t k_dtype, const float* U,
+                          const float* V, int64_t n, int64_t m, void* plan, int64_t ldp,
+                          int32_t plan_dtype, void* stream);
+
+/* uot_kform_cost -- <diag(U) K diag(V), C> without materialising the plan;
+ * each term (U_i K_ij) V_j C_ij is accumulated in an error-free FP32 pair and
+ * the partial sums in FP64.  out_dev: one device double, overwritten.  Async. */
+uot_status uot_kform_cost(const void* K, int64_t ldk, int32_t k_dtype, const float* U,
+                          const float* V, const float* C, int64_t ldc, int64_t n, int64_t m,
+                          double* out_dev, void* stream);
+
 /* Synchronises `stream` and reads the result of the last uot_sinkhorn call
  * that used `workspace` (same n, m, opt).  Returns the device status as a
  * uot_status as uot_sinkhorn does with a non-NULL `out`. */
@@ -149,7 +202,9 @@ uot_status uot_read_result(const void* workspace, int64_t n, int64_t m,
                            const uot_options* opt, void* stream, uot_result* out);
 
 /*
- * uot_cost -- transport cost <P, C> = sum_ij P_ij C_ij, accumulated in FP64.
+ * uot_cost -- transport cost <P, C> = sum_ij P_ij C_ij; each product is
+ * accumulated exactly in an error-free FP32 pair (Dekker / Knuth), and the
+ * partial sums in FP64.
  * plan: n x m of `dtype` (uot_dtype), leading dimension ldp; C: n x m FP32,
  * leading dimension ldc; out_dev: one device double, OVERWRITTEN with the cost
  * (the call zeroes it first on `stream`).  Asynchronous.

@@ -87,7 +87,7 @@ uot_status uot_init_kernel(const float* C, int64_t ldc, void* plan, int64_t ldp,
   if (!(reg > 0.0f) || !std::isfinite(reg)) return UOT_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(plan) % esize(o.dtype) || reinterpret_cast<uintptr_t>(C) % 4)
     return UOT_ERR_INVALID_ARG;
-  cudaError_t e = launch_init(C, ldc, plan, ldp, int(n), int(m), reg, o.dtype,
+  cudaError_t e = launch_init(C, ldc, plan, ldp, int(n), int(m), reg, o.dtype, 1.0f,
                               static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? UOT_OK : UOT_ERR_CUDA;
 }
@@ -109,20 +109,32 @@ uot_status uot_read_result(const void* workspace, int64_t n, int64_t m, const uo
   return status_of(ctl.status);
 }
 
-uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b, int64_t n,
-                        int64_t m, float reg, float reg_m, int32_t iters, double tol,
-                        void* workspace, size_t ws_bytes, const uot_options* opt, void* stream,
-                        uot_result* out) {
+}  // extern "C"
+
+namespace uot {
+
+// Validation, geometry and the launch sequence shared by the in-place plan
+// (kf == false; `mat` is the plan) and the kernel form (kf == true; `mat` is
+// K, read-only, and U / V receive the scalings).
+static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, const float* b,
+                               int64_t n, int64_t m, float reg, float reg_m, int32_t iters,
+                               double tol, float k_log2_scale, float* U, float* V,
+                               void* workspace, size_t ws_bytes, const uot_options* opt,
+                               void* stream, uot_result* out) {
   const uot_options o = resolve(opt);
-  if (!plan || !a || !b || !valid_dims(n, m) || ldp < m || !valid_dtype(o.dtype))
+  if (!mat || !a || !b || !valid_dims(n, m) || ldm < m || !valid_dtype(o.dtype))
     return UOT_ERR_INVALID_ARG;
   if (!(reg > 0.0f) || !std::isfinite(reg) || !(reg_m > 0.0f) || iters < 0)
     return UOT_ERR_INVALID_ARG;
   if (std::isnan(tol) || std::isinf(tol) || !reserved_zero(o)) return UOT_ERR_INVALID_ARG;
   if (o.algo != UOT_ALGO_FUSED && o.algo != UOT_ALGO_MULTIPASS) return UOT_ERR_INVALID_ARG;
   if (o.cluster < 0 || o.cluster > 8 || o.tile < 0) return UOT_ERR_INVALID_ARG;
-  if (reinterpret_cast<uintptr_t>(plan) % esize(o.dtype) ||
+  if (reinterpret_cast<uintptr_t>(mat) % esize(o.dtype) ||
       reinterpret_cast<uintptr_t>(a) % 4 || reinterpret_cast<uintptr_t>(b) % 4)
+    return UOT_ERR_INVALID_ARG;
+  if (kf && (!U || !V || reinterpret_cast<uintptr_t>(U) % 4 || reinterpret_cast<uintptr_t>(V) % 4 ||
+             !std::isfinite(k_log2_scale) || std::fabs(k_log2_scale) > 100.0f ||
+             k_log2_scale != std::nearbyint(k_log2_scale) || o.algo != UOT_ALGO_FUSED))
     return UOT_ERR_INVALID_ARG;
   const WsLayout L = ws_layout(n, m);
   if (!workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(workspace) % 256)
@@ -147,17 +159,21 @@ uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b,
     cs = o.cluster > 0 ? o.cluster : int((m + cfg.cols - 1) / cfg.cols);
     if (cs > 8) return UOT_ERR_UNSUPPORTED;
     if (int64_t(cs) * cfg.cols < m) return UOT_ERR_INVALID_ARG;
-    if (fused_geometry(k, cs, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
+    if (fused_geometry(kf, k, cs, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
   }
 
   if (launch_reset(ws, L, b, M, s) != cudaSuccess) return UOT_ERR_CUDA;
+  if (kf && launch_kform_reset(U, N, std::ldexp(1.0f, -int(std::lround(k_log2_scale))),
+                               reinterpret_cast<float*>(ws + L.beta), M, int(L.mpad), a, b, fi,
+                               reinterpret_cast<double*>(ws + L.log2k), s) != cudaSuccess)
+    return UOT_ERR_CUDA;
   cudaEvent_t ev0 = static_cast<cudaEvent_t>(o.pass_events[0]);
   cudaEvent_t ev1 = static_cast<cudaEvent_t>(o.pass_events[1]);
   if (ev0 && cudaEventRecord(ev0, s) != cudaSuccess) return UOT_ERR_CUDA;
 
   if (o.algo == UOT_ALGO_MULTIPASS) {
     for (int t = 1; t <= iters; ++t) {
-      if (launch_multipass_iter(plan, ldp, N, M, o.dtype, a, b, fi, t, tol, o.check_every, ws, L,
+      if (launch_multipass_iter(mat, ldm, N, M, o.dtype, a, b, fi, t, tol, o.check_every, ws, L,
                                 s, nullptr) != cudaSuccess)
         return UOT_ERR_CUDA;
     }
@@ -165,12 +181,12 @@ uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b,
   } else if (iters == 0) {
     if (ev1 && cudaEventRecord(ev1, s) != cudaSuccess) return UOT_ERR_CUDA;
   } else {
-    const bool tma = reinterpret_cast<uintptr_t>(plan) % 16 == 0 &&
-                     (uint64_t(ldp) * esize(o.dtype)) % 16 == 0;
+    const bool tma = reinterpret_cast<uintptr_t>(mat) % 16 == 0 &&
+                     (uint64_t(ldm) * esize(o.dtype)) % 16 == 0;
 
     FusedArgs A{};
-    A.plan = plan;
-    A.ldp = ldp;
+    A.plan = mat;
+    A.ldp = ldm;
     A.n = N;
     A.m = M;
     A.a = a;
@@ -184,6 +200,8 @@ uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b,
     A.stages = stages;
     A.b_ws = reinterpret_cast<const float*>(ws + L.bws);
     A.dynamic = 1;
+    A.U = U;
+    A.log2k = reinterpret_cast<const double*>(ws + L.log2k);
     A.beta = reinterpret_cast<const float*>(ws + L.beta);
     A.beta_out = reinterpret_cast<float*>(ws + L.beta);
     int* ctr = reinterpret_cast<int*>(ws + L.ctr);
@@ -195,7 +213,7 @@ uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b,
     }
     for (int t = 1; t <= iters; ++t) {
       A.t = t;
-      A.first = t == 1;
+      A.first = !kf && t == 1;  // the kernel form starts from V = 1 in the buffer
       A.check_prev = track && (t - 1) >= 2 && ((t - 1) % o.check_every) == 0;
       A.c_prev = c[(t - 1) % 3];
       A.c_next = c[t % 3];
@@ -207,15 +225,80 @@ uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b,
       A.ctr_clear = ctr + (t + 1) % 3;
       A.arrive = ctr + 3 + t % 3;
       A.arrive_clear = ctr + 3 + (t + 1) % 3;
-      if (fused_launch(k, cs, grid, smem, tma, A, s) != cudaSuccess) return UOT_ERR_CUDA;
+      if (fused_launch(kf, k, cs, grid, smem, tma, A, s) != cudaSuccess) return UOT_ERR_CUDA;
     }
     if (ev1 && cudaEventRecord(ev1, s) != cudaSuccess) return UOT_ERR_CUDA;
-    if (launch_finish(plan, ldp, N, M, o.dtype, b, fi, iters, ws, L, tol, o.check_every, true,
-                      s) != cudaSuccess)
-      return UOT_ERR_CUDA;
+    const cudaError_t e =
+        kf ? launch_kform_finish(V, M, iters, ws, L, tol, s)
+           : launch_finish(mat, ldm, N, M, o.dtype, b, fi, iters, ws, L, tol, o.check_every, true, s);
+    if (e != cudaSuccess) return UOT_ERR_CUDA;
   }
   if (!out) return UOT_OK;
   return uot_read_result(workspace, n, m, &o, stream, out);
+}
+
+}  // namespace uot
+
+extern "C" {
+
+uot_status uot_sinkhorn(void* plan, int64_t ldp, const float* a, const float* b, int64_t n,
+                        int64_t m, float reg, float reg_m, int32_t iters, double tol,
+                        void* workspace, size_t ws_bytes, const uot_options* opt, void* stream,
+                        uot_result* out) {
+  return run_sinkhorn(false, plan, ldp, a, b, n, m, reg, reg_m, iters, tol, 0.0f, nullptr,
+                      nullptr, workspace, ws_bytes, opt, stream, out);
+}
+
+uot_status uot_sinkhorn_kform(const void* K, int64_t ldk, const float* a, const float* b,
+                              int64_t n, int64_t m, float reg, float reg_m, int32_t iters,
+                              double tol, float k_log2_scale, float* U, float* V,
+                              void* workspace, size_t ws_bytes, const uot_options* opt,
+                              void* stream, uot_result* out) {
+  return run_sinkhorn(true, const_cast<void*>(K), ldk, a, b, n, m, reg, reg_m, iters, tol,
+                      k_log2_scale, U, V, workspace, ws_bytes, opt, stream, out);
+}
+
+uot_status uot_init_kernel_scaled(const float* C, int64_t ldc, void* K, int64_t ldk, int64_t n,
+                                  int64_t m, float reg, float log2_scale, const uot_options* opt,
+                                  void* stream) {
+  const uot_options o = resolve(opt);
+  if (!C || !K || !valid_dims(n, m) || ldc < m || ldk < m || !valid_dtype(o.dtype))
+    return UOT_ERR_INVALID_ARG;
+  if (!(reg > 0.0f) || !std::isfinite(reg) || !std::isfinite(log2_scale) ||
+      std::fabs(log2_scale) > 100.0f || log2_scale != std::nearbyint(log2_scale))
+    return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(K) % esize(o.dtype) || reinterpret_cast<uintptr_t>(C) % 4)
+    return UOT_ERR_INVALID_ARG;
+  cudaError_t e = launch_init(C, ldc, K, ldk, int(n), int(m), reg, o.dtype,
+                              std::ldexp(1.0f, int(log2_scale)), static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? UOT_OK : UOT_ERR_CUDA;
+}
+
+uot_status uot_kform_plan(const void* K, int64_t ldk, int32_t k_dtype, const float* U,
+                          const float* V, int64_t n, int64_t m, void* plan, int64_t ldp,
+                          int32_t plan_dtype, void* stream) {
+  if (!K || !U || !V || !plan || !valid_dims(n, m) || ldk < m || ldp < m ||
+      !valid_dtype(k_dtype) || !valid_dtype(plan_dtype))
+    return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(K) % esize(k_dtype) ||
+      reinterpret_cast<uintptr_t>(plan) % esize(plan_dtype))
+    return UOT_ERR_INVALID_ARG;
+  cudaError_t e = launch_kform_plan(K, ldk, k_dtype, U, V, int(n), int(m), plan, ldp, plan_dtype,
+                                    static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? UOT_OK : UOT_ERR_CUDA;
+}
+
+uot_status uot_kform_cost(const void* K, int64_t ldk, int32_t k_dtype, const float* U,
+                          const float* V, const float* C, int64_t ldc, int64_t n, int64_t m,
+                          double* out_dev, void* stream) {
+  if (!K || !U || !V || !C || !out_dev || !valid_dims(n, m) || ldk < m || ldc < m ||
+      !valid_dtype(k_dtype))
+    return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(K) % esize(k_dtype) || reinterpret_cast<uintptr_t>(out_dev) % 8)
+    return UOT_ERR_INVALID_ARG;
+  cudaError_t e = launch_kform_cost(K, ldk, k_dtype, U, V, C, ldc, int(n), int(m), out_dev,
+                                    static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? UOT_OK : UOT_ERR_CUDA;
 }
 
 uot_status uot_cost(const void* plan, int64_t ldp, const float* C, int64_t ldc, int64_t n,

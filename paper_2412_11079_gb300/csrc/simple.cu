@@ -26,15 +26,46 @@ __device__ __forceinline__ float gibbs(float c, float reg) {
   return fmaf(x, e / reg, x);
 }
 
+// P = exp(-C/reg) * scale; scale is a power of two (FP16 kernels are stored
+// scaled into FP16's normal range).
 template <typename T>
 __global__ void __launch_bounds__(TB) init_kernel(const float* __restrict__ C, int64_t ldc,
                                                   T* __restrict__ P, int64_t ldp, int n, int m,
-                                                  float reg) {
+                                                  float reg, float scale) {
   const int j = blockIdx.x * TB + threadIdx.x;
   if (j >= m) return;
   for (int i = blockIdx.y; i < n; i += gridDim.y) {
     const float c = C[int64_t(i) * ldc + j];
-    Elem<T>::store1(P + int64_t(i) * ldp + j, gibbs(c, reg));
+    Elem<T>::store1(P + int64_t(i) * ldp + j, gibbs(c, reg) * scale);
+  }
+}
+
+// Compensated accumulation in a pair of floats (hi + lo): Dekker's exact
+// product through fma, Knuth's TwoSum for the addition.  About 2^-44 relative
+// accuracy for sums of non-negative terms, without the FP64 pipe.
+struct Acc2 {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add_product(float x, float y) {
+    const float p = x * y;
+    const float pe = fmaf(x, y, -p);
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float se = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += se + pe;
+  }
+  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
+__device__ __forceinline__ void block_add_double(double v, double* out) {
+  __shared__ double part[TB / 32];
+  v = warp_sum_d(v);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < TB / 32; ++w) t += part[w];
+    atomicAdd(out, t);
   }
 }
 
@@ -73,20 +104,95 @@ template <typename T>
 __global__ void __launch_bounds__(TB) cost_kernel(const T* __restrict__ P, int64_t ldp,
                                                   const float* __restrict__ C, int64_t ldc, int n,
                                                   int m, double* out) {
-  __shared__ double part[TB / 32];
   const int j = blockIdx.x * TB + threadIdx.x;
-  double acc = 0.0;
+  Acc2 acc;
   if (j < m)
     for (int i = blockIdx.y; i < n; i += gridDim.y)
-      acc += double(Elem<T>::load1(P + int64_t(i) * ldp + j)) * double(C[int64_t(i) * ldc + j]);
-  acc = warp_sum_d(acc);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+      acc.add_product(Elem<T>::load1(P + int64_t(i) * ldp + j), C[int64_t(i) * ldc + j]);
+  block_add_double(acc.value(), out);
+}
+
+// <diag(U) K diag(V), C>: each term (U_i K_ij) V_j is formed in FP32 (two
+// roundings) and accumulated as above.
+template <typename T>
+__global__ void __launch_bounds__(TB) kform_cost_kernel(const T* __restrict__ K, int64_t ldk,
+                                                        const float* __restrict__ U,
+                                                        const float* __restrict__ V,
+                                                        const float* __restrict__ C, int64_t ldc,
+                                                        int n, int m, double* out) {
+  const int j = blockIdx.x * TB + threadIdx.x;
+  Acc2 acc;
+  if (j < m) {
+    const float v = V[j];
+    for (int i = blockIdx.y; i < n; i += gridDim.y)
+      acc.add_product(U[i] * Elem<T>::load1(K + int64_t(i) * ldk + j) * v,
+                      C[int64_t(i) * ldc + j]);
+  }
+  block_add_double(acc.value(), out);
+}
+
+// P = diag(U) K diag(V) in the plan's dtype.
+template <typename TK, typename TP>
+__global__ void __launch_bounds__(TB) kform_plan_kernel(const TK* __restrict__ K, int64_t ldk,
+                                                        const float* __restrict__ U,
+                                                        const float* __restrict__ V, int n, int m,
+                                                        TP* __restrict__ P, int64_t ldp) {
+  const int j = blockIdx.x * TB + threadIdx.x;
+  if (j >= m) return;
+  const float v = V[j];
+  for (int i = blockIdx.y; i < n; i += gridDim.y)
+    Elem<TP>::store1(P + int64_t(i) * ldp + j, U[i] * Elem<TK>::load1(K + int64_t(i) * ldk + j) * v);
+}
+
+// Kernel form: U = u0 (the inverse of K's storage scale), V = 1 (zero-padded).
+__global__ void kform_reset_kernel(float* U, int n, float u0, float* V_ws, int m, int mpad) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gs = gridDim.x * blockDim.x;
+  for (int i = g; i < n; i += gs) U[i] = u0;
+  for (int j = g; j < mpad; j += gs) V_ws[j] = j < m ? 1.0f : 0.0f;
+}
+
+// Kernel form: log2 k, k = (m_a / m_b)^(fi / (2 - fi)) the row factor at the
+// fixed point of the row-then-column rule (0 when a mass is 0 or not finite).
+__global__ void __launch_bounds__(1024) kform_gauge_kernel(const float* a, int n, const float* b,
+                                                           int m, float fi, double* log2k) {
+  __shared__ double part[2][32];
+  double sa = 0.0, sb = 0.0;
+  for (int i = threadIdx.x; i < n; i += 1024) sa += a[i];
+  for (int j = threadIdx.x; j < m; j += 1024) sb += b[j];
+  sa = warp_sum_d(sa);
+  sb = warp_sum_d(sb);
+  if ((threadIdx.x & 31) == 0) {
+    part[0][threadIdx.x >> 5] = sa;
+    part[1][threadIdx.x >> 5] = sb;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < TB / 32; ++w) s += part[w];
-    atomicAdd(out, s);
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < 32; ++w) {
+      ta += part[0][w];
+      tb += part[1][w];
+    }
+    const double f = double(fi);
+    const double L = (f / (2.0 - f)) * log2(ta / tb);
+    *log2k = (ta > 0.0 && tb > 0.0 && isfinite(L)) ? L : 0.0;
   }
+}
+
+// Kernel form: iteration count, last stopping error, V to the caller.
+__global__ void kform_finish_kernel(float* V, const float* V_ws, int m, int iters,
+                                    const double* err_ring, Control* ctl, double tol) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g == 0) {
+    const int done = ctl->done;
+    const int t = done ? ctl->stop_iter : iters;
+    ctl->iters_done = t;
+    if (!done && tol > 0.0 && t >= 2) {
+      const double num = err_ring[(t % 3) * 2], den = err_ring[(t % 3) * 2 + 1];
+      ctl->err = den > 0.0 ? num / den : __longlong_as_double(0x7ff0000000000000ll);
+    }
+  }
+  for (int j = g; j < m; j += gridDim.x * blockDim.x) V[j] = V_ws[j];
 }
 
 __global__ void reset_kernel(Control* ctl, double* err_ring, float* c1, int mpad, const float* b,
@@ -216,10 +322,58 @@ cudaError_t last(int k = 1) {
 }  // namespace
 
 cudaError_t launch_init(const float* C, int64_t ldc, void* P, int64_t ldp, int n, int m,
-                        float reg, int dtype, cudaStream_t s) {
+                        float reg, int dtype, float scale, cudaStream_t s) {
   return by_dtype(dtype, [&](auto z) {
     using T = decltype(z);
-    init_kernel<T><<<col_grid(n, m), TB, 0, s>>>(C, ldc, reinterpret_cast<T*>(P), ldp, n, m, reg);
+    init_kernel<T><<<col_grid(n, m), TB, 0, s>>>(C, ldc, reinterpret_cast<T*>(P), ldp, n, m, reg,
+                                                 scale);
+    return last();
+  });
+}
+
+cudaError_t launch_kform_reset(float* U, int n, float u0, float* V_ws, int m, int mpad,
+                               const float* a, const float* b, float fi, double* log2k,
+                               cudaStream_t s) {
+  const int blocks = (max(n, mpad) + TB - 1) / TB;
+  kform_reset_kernel<<<blocks, TB, 0, s>>>(U, n, u0, V_ws, m, mpad);
+  cudaError_t e = last();
+  if (e != cudaSuccess) return e;
+  kform_gauge_kernel<<<1, 1024, 0, s>>>(a, n, b, m, fi, log2k);
+  return last();
+}
+
+cudaError_t launch_kform_finish(float* V, int m, int iters, const uint8_t* ws, WsLayout L,
+                                double tol, cudaStream_t s) {
+  uint8_t* w = const_cast<uint8_t*>(ws);
+  kform_finish_kernel<<<(m + TB - 1) / TB, TB, 0, s>>>(
+      V, reinterpret_cast<const float*>(w + L.beta), m, iters,
+      reinterpret_cast<const double*>(w + L.err), reinterpret_cast<Control*>(w + L.ctl), tol);
+  return last();
+}
+
+cudaError_t launch_kform_plan(const void* K, int64_t ldk, int k_dtype, const float* U,
+                              const float* V, int n, int m, void* P, int64_t ldp, int p_dtype,
+                              cudaStream_t s) {
+  return by_dtype(k_dtype, [&](auto zk) {
+    using TK = decltype(zk);
+    return by_dtype(p_dtype, [&](auto zp) {
+      using TP = decltype(zp);
+      kform_plan_kernel<TK, TP><<<col_grid(n, m), TB, 0, s>>>(
+          reinterpret_cast<const TK*>(K), ldk, U, V, n, m, reinterpret_cast<TP*>(P), ldp);
+      return last();
+    });
+  });
+}
+
+cudaError_t launch_kform_cost(const void* K, int64_t ldk, int k_dtype, const float* U,
+                              const float* V, const float* C, int64_t ldc, int n, int m,
+                              double* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  return by_dtype(k_dtype, [&](auto z) {
+    using T = decltype(z);
+    kform_cost_kernel<T><<<col_grid(n, m), TB, 0, s>>>(reinterpret_cast<const T*>(K), ldk, U, V,
+                                                       C, ldc, n, m, out);
     return last();
   });
 }

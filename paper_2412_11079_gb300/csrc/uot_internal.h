@@ -38,6 +38,7 @@ struct WsLayout {
   size_t bws;     // float[mpad]: copy of b, zero-padded (aligned vector loads)
   size_t ctr;     // int32[6]: per-pass row counters and arrival counters, rings of 3
   size_t beta;    // float[mpad]: column factors of the last completed pass
+  size_t log2k;   // double: log2 of the fixed-point row factor (kernel-form gauge)
   size_t total;
   int64_t mpad, npad;
 };
@@ -58,6 +59,7 @@ inline WsLayout ws_layout(int64_t n, int64_t m) {
   L.bws = off; off = align256(off + size_t(L.mpad) * 4);
   L.ctr = off; off = align256(off + 6 * sizeof(int32_t));
   L.beta = off; off = align256(off + size_t(L.mpad) * 4);
+  L.log2k = off; off = align256(off + sizeof(double));
   L.total = off;
   return L;
 }
@@ -91,6 +93,8 @@ struct FusedArgs {
   int dynamic;         // 1: dynamic row schedule (single-CTA rows, bulk copies)
   int* arrive;         // CTAs that finished this pass
   int* arrive_clear;   // arrival counter to clear for iteration t+1
+  float* U;            // kernel form: row scalings (read and updated per row)
+  const double* log2k; // kernel form: log2 k for the power-of-two gauge
   const float* beta;   // beta_{t-1}, zero-padded to mpad (read unless first)
   float* beta_out;     // beta_t, written by the last CTAs of this pass
 };
@@ -107,15 +111,26 @@ int fused_num_configs();
 bool fused_config_info(int k, FusedConfig* out);
 // Picks a configuration for dtype/m (tile = 0: automatic; else k+1).
 int fused_pick(int dtype, int64_t m, int tile);
-// Launch geometry for config k at cluster size cs: grid (CTAs), ring depth and
-// dynamic shared memory; returns cudaSuccess or an error.
-cudaError_t fused_geometry(int k, int cs, int n, int* grid, int* stages, size_t* smem);
-cudaError_t fused_launch(int k, int cs, int grid, size_t smem, bool tma, const FusedArgs& args,
-                         cudaStream_t s);
+// Launch geometry for config k (in place, or kernel form when kf) at cluster
+// size cs: grid (CTAs), ring depth and dynamic shared memory.
+cudaError_t fused_geometry(bool kf, int k, int cs, int n, int* grid, int* stages, size_t* smem);
+cudaError_t fused_launch(bool kf, int k, int cs, int grid, size_t smem, bool tma,
+                         const FusedArgs& args, cudaStream_t s);
 
 // Simple kernels (simple.cu).
 cudaError_t launch_init(const float* C, int64_t ldc, void* P, int64_t ldp, int n, int m,
-                        float reg, int dtype, cudaStream_t s);
+                        float reg, int dtype, float scale, cudaStream_t s);
+cudaError_t launch_kform_reset(float* U, int n, float u0, float* V_ws, int m, int mpad,
+                               const float* a, const float* b, float fi, double* log2k,
+                               cudaStream_t s);
+cudaError_t launch_kform_finish(float* V, int m, int iters, const uint8_t* ws, WsLayout L,
+                                double tol, cudaStream_t s);
+cudaError_t launch_kform_plan(const void* K, int64_t ldk, int k_dtype, const float* U,
+                              const float* V, int n, int m, void* P, int64_t ldp, int p_dtype,
+                              cudaStream_t s);
+cudaError_t launch_kform_cost(const void* K, int64_t ldk, int k_dtype, const float* U,
+                              const float* V, const float* C, int64_t ldc, int n, int m,
+                              double* out, cudaStream_t s);
 cudaError_t launch_finish(void* P, int64_t ldp, int n, int m, int dtype, const float* b,
                           float fi, int iters, const uint8_t* ws, WsLayout L, double tol,
                           int check_every, bool beta_ready, cudaStream_t s);

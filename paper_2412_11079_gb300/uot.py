@@ -65,6 +65,13 @@ SIGNATURES = {
     "uot_read_result": (ctypes.c_int, [_P, _I64, _I64, ctypes.POINTER(UotOptions), _P,
                                        ctypes.POINTER(UotResult)]),
     "uot_cost": (ctypes.c_int, [_P, _I64, _P, _I64, _I64, _I64, _I32, _P, _P]),
+    "uot_init_kernel_scaled": (ctypes.c_int, [_P, _I64, _P, _I64, _I64, _I64, _F, _F,
+                                              ctypes.POINTER(UotOptions), _P]),
+    "uot_sinkhorn_kform": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _D, _F,
+                                          _P, _P, _P, _SZ, ctypes.POINTER(UotOptions), _P,
+                                          ctypes.POINTER(UotResult)]),
+    "uot_kform_plan": (ctypes.c_int, [_P, _I64, _I32, _P, _P, _I64, _I64, _P, _I64, _I32, _P]),
+    "uot_kform_cost": (ctypes.c_int, [_P, _I64, _I32, _P, _P, _P, _I64, _I64, _I64, _P, _P]),
     "uot_sinkhorn_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _D,
                                             ctypes.POINTER(UotOptions), _P,
                                             ctypes.POINTER(UotResult)]),
@@ -184,6 +191,75 @@ def uot_init_kernel(C, plan, reg: float, opt: UotOptions | None = None, stream=N
     pp, ldp = _matrix(plan, "plan")
     _check(load().uot_init_kernel(cp, ldc, pp, ldp, n, m, reg, ctypes.byref(opt),
                                   _stream(stream)), "uot_init_kernel")
+
+
+def uot_init_kernel_scaled(C, K, reg: float, log2_scale: int, opt: UotOptions | None = None,
+                           stream=None):
+    n, m = C.shape
+    if tuple(K.shape) != (n, m) or C.dtype != _torch().float32:
+        raise ValueError("K must have C's shape; C must be float32")
+    opt = opt or options(dtype_code(K.dtype))
+    cp, ldc = _matrix(C, "C")
+    kp, ldk = _matrix(K, "K")
+    _check(load().uot_init_kernel_scaled(cp, ldc, kp, ldk, n, m, reg, float(log2_scale),
+                                         ctypes.byref(opt), _stream(stream)),
+           "uot_init_kernel_scaled")
+
+
+def uot_sinkhorn_kform(K, a, b, reg: float, reg_m: float, iters: int, tol: float = 0.0,
+                       k_log2_scale: int = 0, U=None, V=None, ws=None,
+                       opt: UotOptions | None = None, stream=None, sync: bool = True,
+                       check_status: bool = True):
+    """Kernel-form iteration on read-only K; returns (U, V, SinkhornResult or None)."""
+    torch = _torch()
+    n, m = K.shape
+    opt = opt or options(dtype_code(K.dtype))
+    if opt.dtype != dtype_code(K.dtype):
+        raise ValueError("options dtype does not match K")
+    U = torch.empty(n, dtype=torch.float32, device=K.device) if U is None else U
+    V = torch.empty(m, dtype=torch.float32, device=K.device) if V is None else V
+    if ws is None:
+        ws = workspace(n, m, opt, K.device)
+    kp, ldk = _matrix(K, "K")
+    res = UotResult()
+    st = load().uot_sinkhorn_kform(kp, ldk, _vector(a, "a", n), _vector(b, "b", m), n, m,
+                                   float(reg), float(reg_m), int(iters), float(tol),
+                                   float(k_log2_scale), _vector(U, "U", n), _vector(V, "V", m),
+                                   ws.data_ptr(), ws.numel(), ctypes.byref(opt), _stream(stream),
+                                   ctypes.byref(res) if sync else None)
+    if not sync:
+        _check(st, "uot_sinkhorn_kform")
+        return U, V, None
+    if st not in (UOT_OK, UOT_ERR_NONFINITE, UOT_ERR_ZERO_SUM, UOT_ERR_TIMEOUT) or (
+            check_status and st != UOT_OK):
+        raise UotError(st, "uot_sinkhorn_kform")
+    return U, V, SinkhornResult(res.iters_done, res.dev_status, res.err)
+
+
+def uot_kform_plan(K, U, V, plan=None, stream=None):
+    torch = _torch()
+    n, m = K.shape
+    if plan is None:
+        plan = torch.empty((n, m), dtype=torch.float32, device=K.device)
+    kp, ldk = _matrix(K, "K")
+    pp, ldp = _matrix(plan, "plan")
+    _check(load().uot_kform_plan(kp, ldk, dtype_code(K.dtype), _vector(U, "U", n),
+                                 _vector(V, "V", m), n, m, pp, ldp, dtype_code(plan.dtype),
+                                 _stream(stream)), "uot_kform_plan")
+    return plan
+
+
+def uot_kform_cost(K, U, V, C, out=None, stream=None):
+    torch = _torch()
+    n, m = K.shape
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=K.device)
+    kp, ldk = _matrix(K, "K")
+    cp, ldc = _matrix(C, "C")
+    _check(load().uot_kform_cost(kp, ldk, dtype_code(K.dtype), _vector(U, "U", n),
+                                 _vector(V, "V", m), cp, ldc, n, m, out.data_ptr(),
+                                 _stream(stream)), "uot_kform_cost")
+    return out
 
 
 @dataclass

@@ -111,6 +111,22 @@ def small_case(seed: int = 0, n: int = 1024, m: int = 1024, iters: int = 100) ->
     return uniform2d(seed, n, m, 0.05, 1.0, iters)
 
 
+def uniform2d_device(seed: int, n: int, m: int, device, reg: float = 0.1, reg_m: float = 1.0,
+                     iters: int = 300):
+    """``uniform2d`` with the cost matrix formed on the GPU (torch, FP64 then
+    FP32) for sizes where the host round trip dominates; same seeded points
+    and marginals, C equal to the host version up to the last FP32 bit."""
+    import torch
+    rng = np.random.default_rng(seed)
+    x = torch.from_numpy(rng.random((n, 2))).to(device)
+    y = torch.from_numpy(rng.random((m, 2))).to(device)
+    a = uniform_marginal(rng, n, 1.0)
+    b = uniform_marginal(rng, m, 1.5)
+    C = torch.cdist(x, y).square_().to(torch.float32)
+    return C, torch.from_numpy(a).to(device), torch.from_numpy(b).to(device), \
+        float(np.float32(reg)), float(np.float32(reg_m)), iters
+
+
 def precision_case(seed: int = 0, n: int = 32768, m: int = 32768, iters: int = 300) -> Problem:
     """2-D uniform points, reg 0.1, reg_m 1.0, 300 iterations (N=M=32768 for
     timing; the accuracy check uses N=M=8192 of the same generator)."""

@@ -103,6 +103,19 @@ def test_argument_validation_needs_no_gpu(lib):
     h = lib.uot_cost
     assert h(P, 4, P, 4, 4, 4, 0, None, None) == uot.UOT_ERR_INVALID_ARG
     assert h(P, 2, P, 4, 4, 4, 0, P, None) == uot.UOT_ERR_INVALID_ARG
+    k = lib.uot_sinkhorn_kform
+    # missing U, non-integer storage scale, multi-pass requested
+    assert k(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, 0.0, None, P, P, 1 << 20, ctypes.byref(o),
+             None, None) == uot.UOT_ERR_INVALID_ARG
+    assert k(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, 0.5, P, P, P, 1 << 20, ctypes.byref(o),
+             None, None) == uot.UOT_ERR_INVALID_ARG
+    mp = uot.options(algo=uot.UOT_ALGO_MULTIPASS)
+    assert k(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, 0.0, P, P, P, 1 << 20, ctypes.byref(mp),
+             None, None) == uot.UOT_ERR_INVALID_ARG
+    assert lib.uot_init_kernel_scaled(P, 4, P, 4, 4, 4, 0.1, 0.5, None, None) == \
+        uot.UOT_ERR_INVALID_ARG
+    assert lib.uot_kform_plan(P, 4, 0, None, P, 4, 4, P, 4, 0, None) == uot.UOT_ERR_INVALID_ARG
+    assert lib.uot_kform_cost(P, 4, 9, P, P, P, 4, 4, 4, P, None) == uot.UOT_ERR_INVALID_ARG
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
