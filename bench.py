@@ -242,6 +242,89 @@ def run_precision(args):
                                   f"{args.acc_n}^2", "unit": UNIT, "forms": out}), flush=True)
 
 
+def run_batched(args):
+    """Batched workload: 512 problems, N and M log-uniform in [64, 4096],
+    2-D uniform points, reg in [0.02, 0.2], reg_m log-uniform in [0.1, 10],
+    200 iterations each; one persistent launch (autotuned schedule, captured
+    in a CUDA graph) against a loop of single-problem launches."""
+    import torch
+
+    from paper_2412_11079_gb300 import build, uot, workloads
+    from paper_2412_11079_gb300.batch import Batch, autotune
+
+    build.build()
+    uot.load()
+    probs = workloads.batch_uneven(seed=0, iters=args.iters)
+    B = Batch(probs)
+    best, timings = autotune(B)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        B.init_plans(stream=stream)
+        B.run(stream=stream)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            B.init_plans(stream=stream)
+            B.run(stream=stream)
+    cur = torch.cuda.current_stream()  # replay() launches on the current stream
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for _ in range(args.steps):
+        g.replay()
+    e1.record(cur)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    res = B.results()
+    assert all(r.dev_status == 0 for r in res)
+    elems = B.element_iterations
+    # Loops of single-problem launches on the same problems: the in-place
+    # fused path, and the kernel form (what the batched engine runs).
+    opt = uot.options()
+    wss = [uot.workspace(*pl.shape, opt) for pl in B.plans]
+    UV = [(torch.empty(pl.shape[0], device=pl.device), torch.empty(pl.shape[1], device=pl.device))
+          for pl in B.plans]
+
+    def loop_inplace():
+        for p, C, pl, a, b, ws in zip(probs, B.C, B.plans, B.a, B.b, wss):
+            uot.uot_init_kernel(C, pl, p.reg, opt)
+            uot.uot_sinkhorn(pl, a, b, p.reg, p.reg_m, p.iters, 0.0, ws, opt, sync=False)
+
+    def loop_kform():
+        for p, C, pl, a, b, ws, (U, V) in zip(probs, B.C, B.plans, B.a, B.b, wss, UV):
+            uot.uot_init_kernel(C, pl, p.reg, opt)
+            uot.uot_sinkhorn_kform(pl, a, b, p.reg, p.reg_m, p.iters, 0.0, 0, U, V, ws, opt,
+                                   sync=False)
+            uot.uot_kform_plan(pl, U, V, pl)
+
+    loop_ms = {}
+    for name, fn in (("inplace", loop_inplace), ("kform", loop_kform)):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        loop_ms[name] = e0.elapsed_time(e1)
+    alg_bytes = 4.0 * elems + 8.0 * B.elements  # read K per iteration, final sweep
+    print(json.dumps({
+        "workload": f"batched: {len(probs)} problems, N,M log-uniform [64,4096], "
+                    f"{args.iters} iterations each, FP32",
+        "unit": UNIT, "elements": B.elements, "element_iterations": elems,
+        "batched": {"ms": ms, "elems_per_s": elems / (ms * 1e-3),
+                    "alg_gbs": alg_bytes / (ms * 1e-3) / 1e9,
+                    "tuning": {"stages": best.stages, "max_team": best.max_team,
+                               "target_elems": best.target_elems}},
+        "looped_single_launches": {k: {"ms": v, "elems_per_s": elems / (v * 1e-3)}
+                                   for k, v in loop_ms.items()},
+        "batched_over_loop": {k: v / ms for k, v in loop_ms.items()},
+        "autotune_ms": {f"{k[0]}/{k[1]}/{k[2]:.0e}": v for k, v in timings.items()},
+    }), flush=True)
+
+
 def config_of(args):
     return {"workload": f"single UOT problem N=M={args.n}" if args.n == args.m else
             f"single UOT problem {args.n}x{args.m}",
@@ -263,7 +346,7 @@ def main():
     ap.add_argument("--oracle-iters", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "precision"])
+    ap.add_argument("--workload", default="large", choices=["large", "precision", "batched"])
     ap.add_argument("--acc-n", type=int, default=8192)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -274,6 +357,11 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "batched":
+        if args.iters == 500:
+            args.iters = 200
+        run_batched(args)
         return
     if args.workload == "precision":
         if args.n == 16384 and args.m == 16384:

@@ -248,6 +248,59 @@ uot_status uot_sinkhorn_noalloc(void* plan, int64_t ldp, const float* a, const f
                                 double tol, const uot_options* opt, void* stream,
                                 uot_result* out);
 
+/*
+ * Batched iteration: many independent problems of uneven size in one
+ * persistent launch (Section 2.1 rule, one sweep per iteration as in
+ * Algorithm 1; FP32 plans in place).  Problems are grouped into size classes
+ * served by teams of CTAs (a power of two, more CTAs for larger problems);
+ * inside a team, rows are shared dynamically and the team meets at a bounded
+ * software barrier once per iteration.
+ */
+typedef struct uot_problem {
+  void* plan;        /* device, n x m FP32, row-major; 16-byte aligned, ldp % 4 == 0 */
+  int64_t ldp;       /* leading dimension (elements) */
+  int64_t n, m;      /* 1 <= m <= 4096 */
+  const float* a;    /* device, length n */
+  const float* b;    /* device, length m */
+  float reg, reg_m;  /* fi = reg_m / (reg_m + reg); reg_m = +INFINITY gives fi = 1 */
+  int32_t iters;     /* iterations for this problem (>= 0) */
+  int32_t reserved;  /* must be 0 */
+} uot_problem;
+
+/* Schedule knobs (uot_batch_default_tuning fills the defaults):
+ *   stages        ring depth per CTA (2..8 slots of 16 KB);
+ *   max_team      largest team size (a power of two);
+ *   target_elems  element-iterations per CTA used to size the teams: a
+ *                 problem of N*M*(iters+1) element-iterations gets the
+ *                 smallest power-of-two team with team * target >= work. */
+typedef struct uot_batch_tuning {
+  int32_t stages;
+  int32_t max_team;
+  double target_elems;
+  int32_t reserved[4];
+} uot_batch_tuning;
+
+void uot_batch_default_tuning(uot_batch_tuning* t);
+
+/* Workspace bytes for a batch (0 on bad sizes). */
+size_t uot_batched_workspace_size(const uot_problem* probs, int32_t nprob,
+                                  const uot_options* opt);
+
+/* Validates the host array `probs`, builds the schedule and uploads it, with
+ * the per-problem descriptors, into the caller-owned device workspace
+ * (synchronises `stream` once).  Call again whenever a problem changes. */
+uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uot_options* opt,
+                               const uot_batch_tuning* tuning, void* workspace,
+                               size_t ws_bytes, void* stream);
+
+/* Runs every prepared problem: one reset launch and one persistent launch,
+ * fully asynchronous (capturable in a CUDA graph once prepared). */
+uot_status uot_sinkhorn_batched(void* workspace, void* stream);
+
+/* Synchronises `stream` and copies each problem's result to out[0..nprob). */
+uot_status uot_batched_results(const void* workspace, int32_t nprob, uot_result* out,
+                               void* stream);
+
 /* Description of fused-pass configuration k (0-based), for tuning tools:
  * writes dtype, threads per CTA, 16-byte vectors per thread per row and the
  * columns one CTA covers.  Returns the number of configurations when k < 0 or

@@ -1,0 +1,733 @@
+// Batched Sinkhorn-UOT: many independent problems of uneven size in one
+// persistent launch (the rule of Section 2.1 with Algorithm 1's single sweep
+// per iteration).  Each problem runs in kernel form: during the iterations
+// the plan buffer holds the initial plan K read-only and only the FP32
+// scalings change (plan = diag(U) K diag(V)); the final sweep writes the plan
+// over K.  Compared with rescaling the plan in place this reads 4 instead of
+// moving 8 bytes per element per iteration, and no plan entry accumulates
+// two roundings per iteration (in-place FP32 drifts past 1e-5 on slowly
+// mixing problems after a few hundred iterations).
+//
+// Scheduling.  Problems are sorted into size classes; class c is served by
+// teams of G_c CTAs (G_c a power of two, larger for larger problems).  Teams
+// are aligned blocks of G_c consecutive CTAs, and a CTA walks the classes
+// from the largest team size down: while its team of the current class is
+// complete, the team leader takes the next problem of that class from a
+// largest-first queue (an atomic cursor) and hands it to the members through
+// a mailbox.  When a class queue runs dry the team splits into the teams of
+// the next class.  The host picks the classes (the autotuner varies the
+// target work per CTA and the ring depth).
+//
+// Per problem.  The team's CTAs take rows from a per-iteration counter; a
+// CTA processes R = 256 / GT rows per step, GT threads per row (GT the
+// smallest power of two with GT * 16 >= M), so narrow problems keep all
+// threads busy.  Rows arrive through a ring of shared-memory slots filled by
+// 1-D bulk copies.  Each thread holds the column scalings and column partial
+// sums of its 16 columns in registers; partial sums of the row groups are
+// combined in shared memory and folded into the problem's column sums with
+// vector reductions once per iteration, after which the team meets at a
+// software barrier (bounded spin) and every thread updates the scalings of
+// its own columns.  The final sweep writes diag(U) K diag(V).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "uot_device.cuh"
+#include "uot_internal.h"
+
+namespace uot {
+
+namespace {
+
+constexpr int BT = 256;           // threads per CTA
+constexpr int BKV = 4;            // 16-byte vectors per thread per row
+constexpr int BW = BT * BKV * 4;  // widest row (FP32 columns)
+constexpr int MAX_CLASSES = 8;
+constexpr int MAX_STAGES = 8;
+constexpr int SLOT_BYTES = BT * BKV * 16;
+
+struct BatchProblem {
+  float* plan;
+  int64_t ldp;
+  int n, m;
+  const float* a;
+  const float* b;
+  float fi;
+  int iters;
+  int mpad;
+  float* c;       // 3 x mpad column sums of U K (ring)
+  int* ctr;       // 3 row counters (ring)
+  float* U;       // n row scalings
+  double* log2k;  // log2 of the fixed-point row factor (gauge)
+  Control* ctl;
+};
+
+struct BatchSched {
+  int nprob;
+  int nclass;
+  int stages;
+  int class_g[MAX_CLASSES];
+  int class_begin[MAX_CLASSES];
+  int class_end[MAX_CLASSES];
+  int team_base[MAX_CLASSES];  // offset of this class's teams in the team arrays
+  const BatchProblem* probs;
+  const int* order;      // problem indices, by class, largest first
+  int* cursor;           // [MAX_CLASSES] queue positions
+  int* mailbox;          // [teams] problem handed to the team
+  int* bar;              // [teams][2] barrier count, generation
+};
+
+struct BatchHeader {  // at the start of the batched workspace (for inspection)
+  int nprob;
+  int teams;
+  int64_t probs_off, order_off, cursor_off, mailbox_off, bar_off, sched_off;
+  int64_t total;
+};
+
+// Team barrier over G CTAs (G > 1): arrival counter + generation, bounded.
+__device__ bool team_barrier(int* bar, int G, uint32_t& st) {
+  __syncthreads();
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    int* count = bar;
+    int* gen = bar + 1;
+    const int g0 = ld_acquire_gpu(gen);
+    __threadfence();
+    if (atomicAdd(count, 1) == G - 1) {
+      *count = 0;
+      __threadfence();
+      atomicAdd(gen, 1);
+    } else {
+      const uint64_t t0 = global_timer_ns();
+      while (ld_acquire_gpu(gen) == g0) {
+        if (global_timer_ns() - t0 > WAIT_LIMIT_NS) {
+          st |= DEV_TIMEOUT;
+          ok = false;
+          break;
+        }
+      }
+    }
+  }
+  return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+// One sweep over the rows of problem P taken by this CTA.  The plan buffer
+// holds K (the initial plan) during the iterations; the scalings are U (per
+// row, in global memory) and V (per column, in registers: V below).
+// Iteration sweep: r_i = U_i sum_j K_ij V_j, U_i <- U_i alpha_i gauge, column
+// partials of U_i K_ij into c_next.  Final sweep: P_ij = (K_ij V_j) U_i
+// written over K.
+__device__ void sweep(const BatchProblem& P, bool finish, const float (&V)[BKV][4], float gauge,
+                      int* ctr, float* c_next, int stages, unsigned char* ring, uint64_t* full,
+                      int* slot_rows, float* scratch, int& qbase, uint32_t& st, bool& broken) {
+  const int tid = threadIdx.x;
+  const int m = P.m, n = P.n;
+  const int c4 = (m + 3) / 4;  // 16-byte chunks per row
+  int gt = 1;
+  while (gt * BKV < c4) gt <<= 1;  // threads per row
+  const int R = BT / gt;           // rows per step
+  const int g = tid / gt, l = tid % gt;
+  const int row_stride = gt * BKV * 16;  // bytes per row in a slot
+  const uint32_t row_bytes = uint32_t((size_t(m) * 4) & ~size_t(15));
+  const int64_t ldp = P.ldp;
+  float* plan = P.plan;
+  const uint64_t policy = policy_evict_first();
+
+  float cacc[BKV][4];
+#pragma unroll
+  for (int k = 0; k < BKV; ++k)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) cacc[k][e] = 0.0f;
+
+  __syncthreads();  // the ring is free (previous sweep finished with it)
+  // Steps are numbered across sweeps (qbase) so the mbarrier phases continue;
+  // every sweep consumes exactly the steps it arms.  Thread 0 takes row
+  // blocks one step ahead so it never waits on the counter.
+  int issued = qbase;
+  int next_base = 0;
+  if (tid == 0) next_base = atomicAdd(ctr, R);
+  auto arm = [&](int q) {
+    const int slot = q % stages;
+    const int base = next_base;
+    if (base < n) next_base = atomicAdd(ctr, R);
+    uint32_t bytes = 0;
+    for (int r = 0; r < R; ++r) {
+      const int row = base + r;
+      const bool ok = row < n;
+      slot_rows[slot * BT + r] = ok ? row : -1;
+      if (ok) bytes += row_bytes;
+    }
+    if (base >= n) {
+      mbar_arrive(&full[slot]);
+      return false;
+    }
+    if (bytes) {
+      mbar_arrive_expect_tx(&full[slot], bytes);
+      for (int r = 0; r < R && base + r < n; ++r)
+        bulk_load(ring + size_t(slot) * SLOT_BYTES + size_t(r) * row_stride,
+                  plan + int64_t(base + r) * ldp, row_bytes, &full[slot], policy);
+    } else {
+      mbar_arrive(&full[slot]);
+    }
+    return true;
+  };
+  bool more = true;
+  if (tid == 0) {
+    // Rows were written through the generic proxy in the previous sweep
+    // (by this team, within this launch); order those writes before the
+    // bulk copies (async proxy) that read them back.
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    for (int q = 0; q < stages && more; ++q) {
+      more = arm(qbase + q);
+      ++issued;
+    }
+  }
+  int q = qbase;
+  for (;; ++q) {
+    const int slot = q % stages;
+    if (!broken && !mbar_wait_bounded(&full[slot], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS)) {
+      broken = true;
+      st |= DEV_TIMEOUT;
+    }
+    const int row0 = *reinterpret_cast<volatile int*>(&slot_rows[slot * BT]);
+    if (row0 < 0) {  // uniform: rows are taken in blocks, first row decides
+      ++q;
+      break;
+    }
+    const int row = *reinterpret_cast<volatile int*>(&slot_rows[slot * BT + g]);
+    const bool live = row >= 0;
+    const unsigned char* srow = ring + size_t(slot) * SLOT_BYTES + size_t(g) * row_stride;
+    float* grow = plan + int64_t(live ? row : 0) * ldp;
+    float x[BKV][4];
+    float s = 0.0f;
+    const float u_old = live ? __ldcg(P.U + row) : 0.0f;
+#pragma unroll
+    for (int k = 0; k < BKV; ++k) {
+      const int ch = l + k * gt;
+      const int cc = ch * 4;
+      if (live && cc + 4 <= m) {
+        Elem<float>::unpack(ld_shared_v4(srow + size_t(ch) * 16), x[k]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[k][e] = (live && cc + e < m) ? grow[cc + e] : 0.0f;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) s = fmaf(x[k][e], V[k][e], s);
+    }
+    // Row sum over the gt threads of the group: shuffles within the warp,
+    // then shared memory across the group's warps.
+    const int w = min(gt, 32);
+    for (int o = w >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    float* red = scratch + (q & 1) * (BT / 32);
+    if (gt > 32 && (tid & 31) == 0) red[tid >> 5] = s;
+    const int anyb = __syncthreads_or(broken ? 1 : 0);
+    if (anyb) {
+      broken = true;
+      st |= DEV_TIMEOUT;
+      break;
+    }
+    if (tid == 0 && more) {
+      more = arm(issued);
+      ++issued;
+    }
+    if (gt > 32) {
+      const int wpg = gt / 32, w0 = (g * gt) / 32;
+      s = 0.0f;
+      for (int k = 0; k < wpg; ++k) s += red[w0 + k];
+    }
+    if (!live) continue;
+    if (finish) {
+#pragma unroll
+      for (int k = 0; k < BKV; ++k) {
+        const int cc = (l + k * gt) * 4;
+        float y[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) y[e] = (x[k][e] * V[k][e]) * u_old;
+        if (cc + 4 <= m) {
+          st_global_cs_v4(grow + cc, Elem<float>::pack(y));
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (cc + e < m) grow[cc + e] = y[e];
+        }
+      }
+      continue;
+    }
+    const float u_new = u_old * rescale_factor(__ldg(P.a + row), u_old * s, P.fi, st) * gauge;
+    if (l == 0) P.U[row] = u_new;
+#pragma unroll
+    for (int k = 0; k < BKV; ++k)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) cacc[k][e] = fmaf(u_new, x[k][e], cacc[k][e]);
+  }
+  qbase = q;
+  // Writer side of the same ordering: every thread's stores of this sweep
+  // before any later bulk copy of these rows (after the barriers that follow).
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  if (finish) return;
+  // Combine the row groups' column partials (groups own the same columns)
+  // in the now idle ring, then fold them into the column sums.
+  __syncthreads();
+  float* acc = reinterpret_cast<float*>(ring);  // c4 * 4 floats
+  for (int j = tid; j < c4 * 4; j += BT) acc[j] = 0.0f;
+  __syncthreads();
+  for (int gg = 0; gg < R; ++gg) {
+    if (g == gg) {
+#pragma unroll
+      for (int k = 0; k < BKV; ++k) {
+        const int ch = l + k * gt;
+        if (ch < c4)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[ch * 4 + e] += cacc[k][e];
+      }
+    }
+    __syncthreads();
+  }
+  for (int ch = tid; ch < c4; ch += BT) {
+    const int cc = ch * 4;
+    if (cc + 4 <= m) {
+      red_add_v4(c_next + cc, acc[cc], acc[cc + 1], acc[cc + 2], acc[cc + 3]);
+    } else {
+      for (int e = 0; e < 4; ++e)
+        if (cc + e < m) atomicAdd(c_next + cc + e, acc[cc + e]);
+    }
+  }
+  // The ring was written through the generic proxy; order that before the
+  // next bulk copies into it.
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(BT, 2) batched_kernel(const BatchSched S) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int stages = S.stages;
+  unsigned char* ring = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(stages) * SLOT_BYTES);
+  int* slot_rows = reinterpret_cast<int*>(full + MAX_STAGES);
+  float* scratch = reinterpret_cast<float*>(slot_rows + MAX_STAGES * BT);
+  __shared__ int s_prob;
+  const int tid = threadIdx.x;
+  uint32_t st = 0;
+  bool broken = false;
+  int qbase = 0;  // ring steps consumed so far (mbarrier phase bookkeeping)
+
+  if (tid == 0) {
+    for (int s = 0; s < MAX_STAGES; ++s) mbar_init(&full[s], 1);
+    fence_mbar_init();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  for (int c = 0; c < S.nclass && !broken; ++c) {
+    const int G = S.class_g[c];
+    const int team = blockIdx.x / G;
+    if ((team + 1) * G > int(gridDim.x)) continue;  // incomplete team
+    const int rank = blockIdx.x % G;
+    int* bar = S.bar + 2 * (S.team_base[c] + team);
+    int* mbox = S.mailbox + S.team_base[c] + team;
+    while (true) {
+      // The leader takes the next problem of this class and hands it over.
+      if (rank == 0 && tid == 0) {
+        const int pos = atomicAdd(S.cursor + c, 1);
+        const int idx = S.class_begin[c] + pos < S.class_end[c] ? S.order[S.class_begin[c] + pos] : -1;
+        if (G > 1) *reinterpret_cast<volatile int*>(mbox) = idx;
+        s_prob = idx;
+      }
+      if (G > 1) {
+        if (!team_barrier(bar, G, st)) { broken = true; break; }
+        if (tid == 0) s_prob = ld_acquire_gpu(mbox);
+      }
+      __syncthreads();
+      const int pi = s_prob;
+      if (pi < 0) break;
+      const BatchProblem P = S.probs[pi];
+      const int c4 = (P.m + 3) / 4;
+      // Column scalings V of this thread's columns, in registers: every row
+      // group (and every CTA of the team) computes the same values.
+      float V[BKV][4];
+      int gt = 1;
+      while (gt * BKV < c4) gt <<= 1;
+      const int l = tid % gt;
+#pragma unroll
+      for (int k = 0; k < BKV; ++k)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) V[k][e] = ((l + k * gt) * 4 + e < P.m) ? 1.0f : 0.0f;
+      // The scalings drift as U ~ k^t, V ~ k^-t (row factors tend to k at the
+      // fixed point); an exact power of two moves between them every pass.
+      const double L = *P.log2k;
+      float gauge = 1.0f, inv_gauge = 1.0f;
+      for (int t = 1; t <= P.iters + 1 && !broken; ++t) {
+        const bool finish = t == P.iters + 1;
+        // V_j <- V_j (b_j / c_j)^fi 2^-e_{t-1}, c_j = V_j 2^-e_{t-1} sum_i U_i K_ij.
+        if (t > 1) {
+#pragma unroll
+          for (int k = 0; k < BKV; ++k)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int j = (l + k * gt) * 4 + e;
+              if (j < P.m) {
+                const float cj = V[k][e] * __ldcg(P.c + size_t((t - 1) % 3) * P.mpad + j) * inv_gauge;
+                V[k][e] = V[k][e] * rescale_factor(__ldg(P.b + j), cj, P.fi, st) * inv_gauge;
+              }
+            }
+        }
+        if (!finish) {
+          const int ex = int(rint(-double(t) * L) - rint(-double(t - 1) * L));
+          gauge = ldexpf(1.0f, ex);
+          inv_gauge = ldexpf(1.0f, -ex);
+        }
+        // Clear the buffers of iteration t + 1 (leader CTA).
+        if (rank == 0) {
+          float* cl = P.c + size_t((t + 1) % 3) * P.mpad;
+          for (int j = tid; j < P.mpad; j += BT) cl[j] = 0.0f;
+          if (tid == 0) P.ctr[(t + 1) % 3] = 0;
+        }
+        sweep(P, finish, V, gauge, P.ctr + t % 3, P.c + size_t(t % 3) * P.mpad, stages, ring,
+              full, slot_rows, scratch, qbase, st, broken);
+        if (G > 1) {
+          if (!team_barrier(bar, G, st)) { broken = true; break; }
+        } else {
+          __syncthreads();
+        }
+      }
+      if (rank == 0 && tid == 0) P.ctl->iters_done = broken ? 0 : P.iters;
+      if (st && tid == 0) atomicOr(&P.ctl->status, st);
+      st = 0;
+    }
+  }
+}
+
+__global__ void batched_reset_kernel(const BatchProblem* probs, int nprob, int* cursor,
+                                     int* mailbox, int* bar, int nteams) {
+  const int p = blockIdx.x;
+  if (p < nprob) {
+    const BatchProblem P = probs[p];
+    for (int j = threadIdx.x; j < 3 * P.mpad; j += blockDim.x) P.c[j] = 0.0f;
+    if (threadIdx.x < 3) P.ctr[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < P.n; i += blockDim.x) P.U[i] = 1.0f;
+    // log2 k, k = (sum a / sum b)^(fi / (2 - fi)): the fixed-point row factor.
+    __shared__ double part[2][32];
+    double sa = 0.0, sb = 0.0;
+    for (int i = threadIdx.x; i < P.n; i += blockDim.x) sa += P.a[i];
+    for (int j = threadIdx.x; j < P.m; j += blockDim.x) sb += P.b[j];
+    sa = warp_sum_d(sa);
+    sb = warp_sum_d(sb);
+    if ((threadIdx.x & 31) == 0) {
+      part[0][threadIdx.x >> 5] = sa;
+      part[1][threadIdx.x >> 5] = sb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double ta = 0.0, tb = 0.0;
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+        ta += part[0][w];
+        tb += part[1][w];
+      }
+      const double f = double(P.fi);
+      const double Lk = (f / (2.0 - f)) * log2(ta / tb);
+      *P.log2k = (ta > 0.0 && tb > 0.0 && isfinite(Lk)) ? Lk : 0.0;
+    }
+    if (threadIdx.x == 0) {
+      P.ctl->status = 0;
+      P.ctl->done = 0;
+      P.ctl->stop_iter = 0;
+      P.ctl->iters_done = 0;
+      P.ctl->err = __longlong_as_double(0x7ff0000000000000ll);
+    }
+  }
+  if (p == 0) {
+    for (int i = threadIdx.x; i < MAX_CLASSES; i += blockDim.x) cursor[i] = 0;
+    for (int i = threadIdx.x; i < nteams; i += blockDim.x) {
+      mailbox[i] = -1;
+      bar[2 * i] = 0;
+      bar[2 * i + 1] = 0;
+    }
+  }
+}
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t batched_smem(int stages) {
+  return size_t(stages) * SLOT_BYTES + MAX_STAGES * 8 + MAX_STAGES * BT * 4 + 2 * (BT / 32) * 4;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+// Workspace layout: header | BatchSched | problems | order | cursor | mailbox
+// | bar | Control[nprob] | per-problem regions (3 x mpad column sums, counters).
+
+static size_t per_problem_bytes(int64_t n, int64_t m) {
+  const int64_t mpad = (m + 63) & ~int64_t(63);
+  return a256(size_t(3 * mpad) * 4) + 256 + a256(size_t(n) * 4) + 256;
+}
+
+// What a launch needs on the host, recorded by uot_batched_prepare for its
+// workspace (a launch may be captured in a CUDA graph, so it cannot read the
+// device copy back).
+struct HostPlan {
+  const void* ws;
+  int grid, stages, nprob, teams;
+  size_t probs_off, cursor_off, mailbox_off, bar_off, ctl_off;
+  BatchSched sched;
+};
+static std::mutex g_plan_mu;
+static std::vector<HostPlan> g_plans;
+
+static bool find_plan(const void* ws, HostPlan* out) {
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  for (const HostPlan& h : g_plans)
+    if (h.ws == ws) {
+      *out = h;
+      return true;
+    }
+  return false;
+}
+
+static int64_t max_teams_bound(int nprob) { return int64_t(nprob) + 4096; }
+
+}  // namespace uot
+
+using namespace uot;
+
+extern "C" {
+
+size_t uot_batched_workspace_size(const uot_problem* probs, int32_t nprob, const uot_options* opt) {
+  (void)opt;
+  if (!probs || nprob <= 0) return 0;
+  size_t total = a256(sizeof(BatchHeader)) + a256(sizeof(BatchSched)) +
+                 a256(size_t(nprob) * sizeof(BatchProblem)) + a256(size_t(nprob) * 4) +
+                 a256(MAX_CLASSES * 4) + a256(size_t(max_teams_bound(nprob)) * 4) +
+                 a256(size_t(max_teams_bound(nprob)) * 8) + a256(size_t(nprob) * sizeof(Control));
+  for (int i = 0; i < nprob; ++i) {
+    if (probs[i].n < 1 || probs[i].m < 1) return 0;
+    total += per_problem_bytes(probs[i].n, probs[i].m);
+  }
+  return total;
+}
+
+uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uot_options* opt,
+                               const uot_batch_tuning* tuning, void* workspace, size_t ws_bytes,
+                               void* stream) {
+  if (!probs || nprob <= 0) return UOT_ERR_INVALID_ARG;
+  uot_options o;
+  uot_default_options(&o);
+  if (opt) o = *opt;
+  if (o.dtype != UOT_F32 || o.algo != UOT_ALGO_FUSED) return UOT_ERR_UNSUPPORTED;
+  const size_t need = uot_batched_workspace_size(probs, nprob, opt);
+  if (need == 0) return UOT_ERR_INVALID_ARG;
+  if (!workspace || ws_bytes < need || reinterpret_cast<uintptr_t>(workspace) % 256)
+    return UOT_ERR_WORKSPACE;
+  for (int i = 0; i < nprob; ++i) {
+    const uot_problem& q = probs[i];
+    if (!q.plan || !q.a || !q.b || q.m > BW || q.n > INT32_MAX || q.ldp < q.m || q.iters < 0 ||
+        !(q.reg > 0.0f) || !std::isfinite(q.reg) || !(q.reg_m > 0.0f) ||
+        reinterpret_cast<uintptr_t>(q.plan) % 16 || (q.ldp % 4) != 0 ||
+        reinterpret_cast<uintptr_t>(q.a) % 4 || reinterpret_cast<uintptr_t>(q.b) % 4)
+      return UOT_ERR_INVALID_ARG;
+  }
+  uot_batch_tuning tu;
+  uot_batch_default_tuning(&tu);
+  if (tuning) tu = *tuning;
+  if (tu.stages < 2 || tu.stages > MAX_STAGES || tu.target_elems <= 0 || tu.max_team < 1 ||
+      tu.max_team > 1024 || (tu.max_team & (tu.max_team - 1)))
+    return UOT_ERR_INVALID_ARG;
+
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return UOT_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return UOT_ERR_CUDA;
+  const size_t smem = batched_smem(tu.stages);
+  if (cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(smem)) != cudaSuccess)
+    return UOT_ERR_CUDA;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel, BT, smem) !=
+          cudaSuccess ||
+      occ < 1)
+    return UOT_ERR_CUDA;
+  const int grid = occ * sms;
+
+  // Classes: team size = clamp(next power of two of N*M*iters / target), so
+  // every CTA of a team gets about `target_elems` element-iterations.
+  std::vector<int> gsize(nprob);
+  std::vector<double> work(nprob);
+  for (int i = 0; i < nprob; ++i) {
+    work[i] = double(probs[i].n) * double(probs[i].m) * double(probs[i].iters + 1);
+    int g = 1;
+    while (g < tu.max_team && g * 2 <= grid && double(g) * tu.target_elems < work[i]) g <<= 1;
+    gsize[i] = g;
+  }
+  std::vector<int> classes;
+  for (int g = tu.max_team; g >= 1; g >>= 1)
+    for (int i = 0; i < nprob; ++i)
+      if (gsize[i] == g) {
+        classes.push_back(g);
+        break;
+      }
+  if (int(classes.size()) > MAX_CLASSES) {  // merge the smallest classes into size 1
+    for (int i = 0; i < nprob; ++i)
+      if (gsize[i] < classes[MAX_CLASSES - 1]) gsize[i] = classes[MAX_CLASSES - 1];
+    classes.resize(MAX_CLASSES);
+  }
+
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  std::vector<uint8_t> host(need, 0);
+  size_t off = 0;
+  BatchHeader* H = reinterpret_cast<BatchHeader*>(host.data());
+  off = a256(sizeof(BatchHeader));
+  const size_t sched_off = off;
+  off += a256(sizeof(BatchSched));
+  const size_t probs_off = off;
+  off += a256(size_t(nprob) * sizeof(BatchProblem));
+  const size_t order_off = off;
+  off += a256(size_t(nprob) * 4);
+  const size_t cursor_off = off;
+  off += a256(MAX_CLASSES * 4);
+  const size_t mailbox_off = off;
+  off += a256(size_t(max_teams_bound(nprob)) * 4);
+  const size_t bar_off = off;
+  off += a256(size_t(max_teams_bound(nprob)) * 8);
+  const size_t ctl_off = off;
+  off += a256(size_t(nprob) * sizeof(Control));
+
+  BatchProblem* P = reinterpret_cast<BatchProblem*>(host.data() + probs_off);
+  for (int i = 0; i < nprob; ++i) {
+    const uot_problem& q = probs[i];
+    BatchProblem& d = P[i];
+    d.plan = static_cast<float*>(q.plan);
+    d.ldp = q.ldp;
+    d.n = int(q.n);
+    d.m = int(q.m);
+    d.a = q.a;
+    d.b = q.b;
+    const double fi = std::isinf(q.reg_m) ? 1.0
+                                          : double(q.reg_m) / (double(q.reg_m) + double(q.reg));
+    d.fi = float(fi);
+    d.iters = q.iters;
+    d.mpad = int((q.m + 63) & ~int64_t(63));
+    d.ctl = reinterpret_cast<Control*>(ws + ctl_off) + i;
+    d.c = reinterpret_cast<float*>(ws + off);
+    off += a256(size_t(3) * d.mpad * 4);
+    d.ctr = reinterpret_cast<int*>(ws + off);
+    off += 256;
+    d.U = reinterpret_cast<float*>(ws + off);
+    off += a256(size_t(q.n) * 4);
+    d.log2k = reinterpret_cast<double*>(ws + off);
+    off += 256;
+  }
+  int* order = reinterpret_cast<int*>(host.data() + order_off);
+  BatchSched S{};
+  S.nprob = nprob;
+  S.nclass = int(classes.size());
+  S.stages = tu.stages;
+  int pos = 0, teams = 0;
+  for (int c = 0; c < S.nclass; ++c) {
+    const int g = classes[c];
+    std::vector<int> idx;
+    for (int i = 0; i < nprob; ++i)
+      if (gsize[i] == g) idx.push_back(i);
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return work[x] > work[y]; });
+    S.class_g[c] = g;
+    S.class_begin[c] = pos;
+    for (int i : idx) order[pos++] = i;
+    S.class_end[c] = pos;
+    S.team_base[c] = teams;
+    teams += grid / g;
+  }
+  if (teams > max_teams_bound(nprob)) return UOT_ERR_UNSUPPORTED;
+  S.probs = reinterpret_cast<const BatchProblem*>(ws + probs_off);
+  S.order = reinterpret_cast<const int*>(ws + order_off);
+  S.cursor = reinterpret_cast<int*>(ws + cursor_off);
+  S.mailbox = reinterpret_cast<int*>(ws + mailbox_off);
+  S.bar = reinterpret_cast<int*>(ws + bar_off);
+  std::memcpy(host.data() + sched_off, &S, sizeof(S));
+  H->nprob = nprob;
+  H->teams = teams;
+  H->probs_off = int64_t(probs_off);
+  H->order_off = int64_t(order_off);
+  H->cursor_off = int64_t(cursor_off);
+  H->mailbox_off = int64_t(mailbox_off);
+  H->bar_off = int64_t(bar_off);
+  H->sched_off = int64_t(sched_off);
+  H->total = int64_t(off);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(ws, host.data(), off, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return UOT_ERR_CUDA;
+  // The host copy must outlive the asynchronous transfer.
+  if (cudaStreamSynchronize(s) != cudaSuccess) return UOT_ERR_CUDA;
+  HostPlan hp{workspace, grid, tu.stages, nprob, teams, probs_off, cursor_off,
+              mailbox_off,   bar_off, ctl_off,  S};
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  for (HostPlan& h : g_plans)
+    if (h.ws == workspace) {
+      h = hp;
+      return UOT_OK;
+    }
+  g_plans.push_back(hp);
+  return UOT_OK;
+}
+
+uot_status uot_sinkhorn_batched(void* workspace, void* stream) {
+  HostPlan hp;
+  if (!workspace || !find_plan(workspace, &hp)) return UOT_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  batched_reset_kernel<<<std::max(hp.nprob, 1), 256, 0, s>>>(
+      reinterpret_cast<const BatchProblem*>(ws + hp.probs_off), hp.nprob,
+      reinterpret_cast<int*>(ws + hp.cursor_off), reinterpret_cast<int*>(ws + hp.mailbox_off),
+      reinterpret_cast<int*>(ws + hp.bar_off), hp.teams);
+  if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
+  count_launch();
+  // All CTAs must be resident at once (team barriers): the grid is the
+  // occupancy recorded at preparation, re-checked here.
+  int dev = 0, sms = 0, occ = 0;
+  const size_t smem = batched_smem(hp.stages);
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel, BT, smem) != cudaSuccess)
+    return UOT_ERR_CUDA;
+  if (occ * sms < hp.grid) return UOT_ERR_UNSUPPORTED;
+  batched_kernel<<<hp.grid, BT, smem, s>>>(hp.sched);
+  if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
+  count_launch();
+  return UOT_OK;
+}
+
+uot_status uot_batched_results(const void* workspace, int32_t nprob, uot_result* out,
+                               void* stream) {
+  HostPlan hp;
+  if (!workspace || !out || !find_plan(workspace, &hp) || nprob != hp.nprob)
+    return UOT_ERR_INVALID_ARG;
+  std::vector<Control> ctl(static_cast<size_t>(nprob));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(ctl.data(), static_cast<const uint8_t*>(workspace) + hp.ctl_off,
+                      size_t(nprob) * sizeof(Control), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return UOT_ERR_CUDA;
+  uint32_t any = 0;
+  for (int i = 0; i < nprob; ++i) {
+    out[i].iters_done = ctl[i].iters_done;
+    out[i].dev_status = ctl[i].status;
+    out[i].err = ctl[i].err;
+    any |= ctl[i].status;
+  }
+  if (any & UOT_DEV_TIMEOUT) return UOT_ERR_TIMEOUT;
+  if (any & UOT_DEV_NONFINITE) return UOT_ERR_NONFINITE;
+  if (any & UOT_DEV_ZERO_SUM) return UOT_ERR_ZERO_SUM;
+  return UOT_OK;
+}
+
+void uot_batch_default_tuning(uot_batch_tuning* t) {
+  if (!t) return;
+  std::memset(t, 0, sizeof(*t));
+  t->stages = 4;
+  t->max_team = 32;
+  t->target_elems = 4.0e7;
+}
+
+}  // extern "C"

@@ -42,6 +42,18 @@ class UotResult(ctypes.Structure):
                 ("err", ctypes.c_double)]
 
 
+class UotProblem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("ldp", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("m", ctypes.c_int64), ("a", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("reg", ctypes.c_float), ("reg_m", ctypes.c_float), ("iters", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class UotBatchTuning(ctypes.Structure):
+    _fields_ = [("stages", ctypes.c_int32), ("max_team", ctypes.c_int32),
+                ("target_elems", ctypes.c_double), ("reserved", ctypes.c_int32 * 4)]
+
+
 class UotError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -75,6 +87,14 @@ SIGNATURES = {
     "uot_sinkhorn_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _D,
                                             ctypes.POINTER(UotOptions), _P,
                                             ctypes.POINTER(UotResult)]),
+    "uot_batch_default_tuning": (None, [ctypes.POINTER(UotBatchTuning)]),
+    "uot_batched_workspace_size": (_SZ, [ctypes.POINTER(UotProblem), _I32,
+                                         ctypes.POINTER(UotOptions)]),
+    "uot_batched_prepare": (ctypes.c_int, [ctypes.POINTER(UotProblem), _I32,
+                                           ctypes.POINTER(UotOptions),
+                                           ctypes.POINTER(UotBatchTuning), _P, _SZ, _P]),
+    "uot_sinkhorn_batched": (ctypes.c_int, [_P, _P]),
+    "uot_batched_results": (ctypes.c_int, [_P, _I32, ctypes.POINTER(UotResult), _P]),
     "uot_fused_config": (_I32, [_I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                 ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
 }
@@ -173,6 +193,16 @@ def workspace(n: int, m: int, opt: UotOptions | None = None, device=None):
     size = uot_workspace_size(n, m, opt)
     if size == 0:
         raise ValueError("bad problem size")
+    buf = torch.empty(size + 256, dtype=torch.uint8, device=device or "cuda")
+    off = (-buf.data_ptr()) % 256
+    return buf[off:off + size]
+
+
+def workspace_bytes(size: int, device=None):
+    """A 256-byte aligned device byte buffer of `size` bytes."""
+    torch = _torch()
+    if size <= 0:
+        raise ValueError("bad workspace size")
     buf = torch.empty(size + 256, dtype=torch.uint8, device=device or "cuda")
     off = (-buf.data_ptr()) % 256
     return buf[off:off + size]
@@ -356,3 +386,41 @@ def solve(C, a, b, reg: float, reg_m: float = math.inf, iters: int = 100, tol: f
     res = uot_sinkhorn(plan, a, b, reg, reg_m, iters, tol, opt=opt, stream=stream)
     cost = uot_cost(plan, C, stream=stream)
     return plan, cost, res
+
+
+def batch_tuning(stages: int | None = None, max_team: int | None = None,
+                 target_elems: float | None = None) -> UotBatchTuning:
+    t = UotBatchTuning()
+    load().uot_batch_default_tuning(ctypes.byref(t))
+    if stages is not None:
+        t.stages = stages
+    if max_team is not None:
+        t.max_team = max_team
+    if target_elems is not None:
+        t.target_elems = target_elems
+    return t
+
+
+def uot_batched_workspace_size(probs) -> int:
+    arr = (UotProblem * len(probs))(*probs)
+    return int(load().uot_batched_workspace_size(arr, len(probs), None))
+
+
+def uot_batched_prepare(probs, ws, tuning: UotBatchTuning | None = None, stream=None):
+    arr = (UotProblem * len(probs))(*probs)
+    _check(load().uot_batched_prepare(arr, len(probs), None,
+                                      ctypes.byref(tuning) if tuning else None, ws.data_ptr(),
+                                      ws.numel(), _stream(stream)), "uot_batched_prepare")
+
+
+def uot_sinkhorn_batched(ws, stream=None):
+    _check(load().uot_sinkhorn_batched(ws.data_ptr(), _stream(stream)), "uot_sinkhorn_batched")
+
+
+def uot_batched_results(ws, nprob: int, stream=None, check_status: bool = True):
+    out = (UotResult * nprob)()
+    st = load().uot_batched_results(ws.data_ptr(), nprob, out, _stream(stream))
+    if st not in (UOT_OK, UOT_ERR_NONFINITE, UOT_ERR_ZERO_SUM, UOT_ERR_TIMEOUT) or (
+            check_status and st != UOT_OK):
+        raise UotError(st, "uot_batched_results")
+    return [SinkhornResult(r.iters_done, r.dev_status, r.err) for r in out]

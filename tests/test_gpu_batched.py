@@ -1,0 +1,142 @@
+"""Batched persistent iteration (uot_sinkhorn_batched) against the FP64 oracle,
+problem by problem, at the FP32 tolerance (1e-5 relative per plan entry)."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_11079_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def uot():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_11079_gb300 import build, uot as u
+    build.build()
+    u.load()
+    return u
+
+
+def rel_err(got, ref):
+    floor = 1e-6 * np.abs(ref).max()
+    return float(np.max(np.abs(np.asarray(got, np.float64) - ref) / np.maximum(np.abs(ref), floor)))
+
+
+def mixed_problems():
+    shapes = [(1, 1), (3, 5), (64, 65), (17, 4096), (2000, 300), (777, 1025), (129, 2049),
+              (500, 64), (63, 1000), (1024, 1024), (31, 33), (4000, 129)]
+    out = []
+    rng = np.random.default_rng(7)
+    for k, (n, m) in enumerate(shapes):
+        reg = float(rng.uniform(0.05, 0.3))
+        reg_m = math.inf if k % 5 == 4 else float(np.exp(rng.uniform(np.log(0.1), np.log(10))))
+        iters = [0, 1, 7, 40, 25][k % 5]
+        out.append(workloads.uniform2d(seed=100 + k, n=n, m=m, reg=reg, reg_m=reg_m, iters=iters))
+    return out
+
+
+def check_batch(uot, problems, tuning=None):
+    from paper_2412_11079_gb300.batch import Batch
+    B = Batch(problems)
+    B.init_plans()
+    B.prepare(tuning)
+    B.run()
+    res = B.results()
+    for p, plan, r in zip(problems, B.plans, res):
+        ref = oracle.sinkhorn(oracle.init_plan(p.C, p.reg), p.a, p.b, p.reg, p.reg_m, p.iters)
+        assert r.iters_done == p.iters and r.dev_status == 0
+        assert rel_err(plan.double().cpu().numpy(), ref.plan) <= FP32_TOL, (p.name, p.iters)
+    return B
+
+
+def test_mixed_batch_matches_oracle(uot):
+    check_batch(uot, mixed_problems())
+
+
+def test_large_teams_on_small_problems(uot):
+    """Tiny target work per CTA forces multi-CTA teams (software barriers,
+    shared row counters) even for small problems."""
+    check_batch(uot, mixed_problems(), uot.batch_tuning(stages=3, max_team=64, target_elems=1e4))
+
+
+def test_single_cta_teams_only(uot):
+    check_batch(uot, mixed_problems()[:8], uot.batch_tuning(stages=8, max_team=1, target_elems=1e12))
+
+
+def test_batched_run_captured_in_graph(uot):
+    from paper_2412_11079_gb300.batch import Batch
+    probs = mixed_problems()[:6]
+    B = Batch(probs)
+    B.init_plans()
+    B.prepare()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        B.run(stream=s)  # warm-up outside capture
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            B.init_plans(stream=s)
+            B.run(stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    for p, plan in zip(probs, B.plans):
+        ref = oracle.sinkhorn(oracle.init_plan(p.C, p.reg), p.a, p.b, p.reg, p.reg_m, p.iters)
+        assert rel_err(plan.double().cpu().numpy(), ref.plan) <= FP32_TOL
+
+
+def test_prepare_rejects_unsupported(uot):
+    from paper_2412_11079_gb300.batch import Batch
+    p = workloads.uniform2d(seed=1, n=4, m=4100, iters=1)
+    with pytest.raises(uot.UotError):
+        B = Batch([p])
+        B.prepare()
+    q = workloads.uniform2d(seed=2, n=5, m=6, iters=1)
+    B = Batch([q])
+    B.descs[0].ldp = 7  # rows no longer 16-byte aligned
+    with pytest.raises(uot.UotError):
+        B.prepare()
+
+
+def test_autotune_picks_a_working_schedule(uot):
+    from paper_2412_11079_gb300.batch import Batch, autotune
+    probs = mixed_problems()[:5]
+    B = Batch(probs)
+    cands = [uot.batch_tuning(3, 8, 1e6), uot.batch_tuning(4, 32, 4e7)]
+    best, timings = autotune(B, cands)
+    assert len(timings) == 2 and best is not None
+    B.init_plans()
+    B.run()
+    for p, plan in zip(probs, B.plans):
+        ref = oracle.sinkhorn(oracle.init_plan(p.C, p.reg), p.a, p.b, p.reg, p.reg_m, p.iters)
+        assert rel_err(plan.double().cpu().numpy(), ref.plan) <= FP32_TOL
+
+
+@pytest.mark.slow
+def test_uneven_batch_full_size_sampled(uot):
+    """512 problems, N and M log-uniform in [64, 4096], 200 iterations each,
+    in the launch configuration the benchmark uses (autotuned schedule); a
+    sample of problems is compared with the oracle."""
+    from paper_2412_11079_gb300.batch import Batch, autotune
+    probs = workloads.batch_uneven(seed=0)
+    B = Batch(probs)
+    autotune(B, [uot.batch_tuning(4, 32, 4e7), uot.batch_tuning(4, 64, 1e7)])
+    B.init_plans()
+    B.run()
+    res = B.results()
+    assert all(r.iters_done == 200 and r.dev_status == 0 for r in res)
+    sizes = np.array([p.C.size for p in probs])
+    order = np.argsort(sizes)
+    sample = list(order[:3]) + list(order[len(order) // 2:len(order) // 2 + 2]) + [order[-60]]
+    for i in sample:
+        p = probs[i]
+        ref = oracle.sinkhorn(oracle.init_plan(p.C, p.reg), p.a, p.b, p.reg, p.reg_m, p.iters)
+        assert rel_err(B.plans[i].double().cpu().numpy(), ref.plan) <= FP32_TOL, p.name
