@@ -325,6 +325,100 @@ def run_batched(args):
     }), flush=True)
 
 
+def run_grad(args):
+    """Differentiation workload: 32 problems N=M=2048 (16-D Gaussian clouds,
+    C/max, reg 0.05, reg_m 1.0), 200 unrolled iterations, forward (kernel
+    form with history) + adjoint backward of <P, C> w.r.t. C, a, b; the
+    whole batch captured in one CUDA graph."""
+    import torch
+
+    import oracle
+    from paper_2412_11079_gb300 import build, uot, workloads
+
+    build.build()
+    uot.load()
+    dev = torch.device("cuda", 0)
+    probs = workloads.grad_batch(seed=0, count=args.batch, n=args.n, m=args.m, iters=args.iters)
+    n, m, iters = args.n, args.m, args.iters
+    ld = (m + 3) // 4 * 4
+    bufs = []
+    for p in probs:
+        C = torch.from_numpy(p.C).to(dev)
+        a = torch.from_numpy(p.a).to(dev)
+        b = torch.from_numpy(p.b).to(dev)
+        K = torch.empty((n, ld), device=dev)[:, :m]
+        U, V = torch.empty(n, device=dev), torch.empty(m, device=dev)
+        hist = uot.workspace_bytes(int(uot.load().uot_grad_hist_size(n, m, iters)), dev)
+        ws = uot.workspace(n, m, None, dev)
+        bws = uot.workspace_bytes(int(uot.load().uot_backward_workspace_size(n, m)), dev)
+        dC = torch.empty((n, ld), device=dev)[:, :m]
+        da, db = torch.empty(n, device=dev), torch.empty(m, device=dev)
+        cost = torch.empty(1, dtype=torch.float64, device=dev)
+        bufs.append((p, C, a, b, K, U, V, hist, ws, bws, dC, da, db, cost))
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+
+    def step(s):
+        for (p, C, a, b, K, U, V, hist, ws, bws, dC, da, db, cost) in bufs:
+            uot.uot_init_kernel(C, K, p.reg, stream=s)
+            uot.uot_sinkhorn_kform_save(K, a, b, p.reg, p.reg_m, iters, U, V, hist, ws, s)
+            uot.uot_kform_cost(K, U, V, C, cost, s)
+            uot.uot_sinkhorn_backward(K, C, a, b, p.reg, p.reg_m, iters, hist, 1.0, dC, da, db,
+                                      bws, s)
+
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        step(stream)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            step(stream)
+    cur = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for _ in range(args.steps):
+        g.replay()
+    e1.record(cur)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    elems = len(probs) * n * m * iters
+    # Gradient errors of the first problem at the full size, against the
+    # oracle's FP64 adjoint on a few iterations (the full 200 would take
+    # minutes on the host); the long runs are covered by the GPU tests.
+    q = workloads.grad_batch(seed=0, count=1, n=n, m=m, iters=args.grad_check_iters)[0]
+    Cq = torch.from_numpy(q.C).to(dev).requires_grad_(True)
+    aq = torch.from_numpy(q.a).to(dev).requires_grad_(True)
+    bq = torch.from_numpy(q.b).to(dev).requires_grad_(True)
+    from paper_2412_11079_gb300.autograd import sinkhorn_cost
+    sinkhorn_cost(Cq, aq, bq, q.reg, q.reg_m, q.iters).backward()
+    rv, rdC, rda, rdb = oracle.sinkhorn_grad(q.C, q.a, q.b, q.reg, q.reg_m, q.iters)
+    def rel(x, r):
+        return float(np.max(np.abs(x.double().cpu().numpy() - r)) / np.max(np.abs(r)))
+    # forward-only timing of the same batch
+    def fwd(s):
+        for (p, C, a, b, K, U, V, hist, ws, bws, dC, da, db, cost) in bufs:
+            uot.uot_init_kernel(C, K, p.reg, stream=s)
+            uot.uot_sinkhorn_kform_save(K, a, b, p.reg, p.reg_m, iters, U, V, hist, ws, s)
+    with torch.cuda.stream(stream):
+        fwd(stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fwd(stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    print(json.dumps({
+        "workload": f"grad: {len(probs)} problems N=M={n}, {iters} iterations, forward + adjoint",
+        "unit": UNIT, "ms_per_step": ms, "elems_per_s": elems / (ms * 1e-3),
+        "forward_ms": fwd_ms, "backward_ms": ms - fwd_ms,
+        "alg_gbs": (elems * (4.0 + 12.0)) / (ms * 1e-3) / 1e9,
+        "grad_rel_err": {"iters": q.iters, "dC": rel(Cq.grad, rdC), "da": rel(aq.grad, rda),
+                         "db": rel(bq.grad, rdb)},
+    }), flush=True)
+
+
 def config_of(args):
     return {"workload": f"single UOT problem N=M={args.n}" if args.n == args.m else
             f"single UOT problem {args.n}x{args.m}",
@@ -346,7 +440,10 @@ def main():
     ap.add_argument("--oracle-iters", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "precision", "batched"])
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "precision", "batched", "grad"])
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--grad-check-iters", type=int, default=5)
     ap.add_argument("--acc-n", type=int, default=8192)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -357,6 +454,13 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "grad":
+        if args.n == 16384 and args.m == 16384:
+            args.n = args.m = 2048
+        if args.iters == 500:
+            args.iters = 200
+        run_grad(args)
         return
     if args.workload == "batched":
         if args.iters == 500:

@@ -195,6 +195,48 @@ uot_status uot_kform_cost(const void* K, int64_t ldk, int32_t k_dtype, const flo
                           const float* V, const float* C, int64_t ldc, int64_t n, int64_t m,
                           double* out_dev, void* stream);
 
+/*
+ * Differentiation of the unrolled iteration (the paper has no adjoint; this
+ * is reverse mode through the Section 2.1 rule in log space).
+ *
+ * uot_grad_hist_size -- bytes of the history a solve of `iters` iterations
+ * keeps for its adjoint: the scalings U_t, V_t and the row/column sums r_t,
+ * c_t for every t (about (iters + 1) * 8 * (n + m) bytes).
+ *
+ * uot_sinkhorn_kform_save -- uot_sinkhorn_kform (fixed `iters`, no stopping
+ * rule) that also fills `hist` (device, caller-owned, 256-byte aligned,
+ * >= uot_grad_hist_size bytes).
+ */
+size_t uot_grad_hist_size(int64_t n, int64_t m, int32_t iters);
+uot_status uot_sinkhorn_kform_save(const void* K, int64_t ldk, const float* a, const float* b,
+                                   int64_t n, int64_t m, float reg, float reg_m, int32_t iters,
+                                   float k_log2_scale, float* U, float* V, void* hist,
+                                   size_t hist_bytes, void* workspace, size_t ws_bytes,
+                                   const uot_options* opt, void* stream, uot_result* out);
+
+/*
+ * uot_sinkhorn_backward -- gradients of L = <P_T, C> times grad_out with
+ * respect to C (dC, n x m FP32, leading dimension lddc), a (da, n) and b
+ * (db, m), for the solve recorded in `hist` by uot_sinkhorn_kform_save with
+ * FP32 K = exp(-C/reg) (k_log2_scale 0) and the same iters, reg, reg_m.
+ * Reverse steps t = T..1, one sweep each: Q_t = diag(U_t) K diag(V_{t-1})
+ * and R_t = diag(U_{t-1}) K diag(V_{t-1}) are recomputed per row, the row
+ * adjoint F and column adjoint G follow
+ *   w = -fi G / c_t,  db += fi G / b,  F += Q_t w,  G = (1 - fi) G,
+ *   z = -fi F / r_t,  da += fi F / a,  G += R_t^T z, F = (1 - fi) F,
+ * with dl += Q_t * w + R_t * z accumulated in the dC buffer, starting from
+ * dl = P_T * C; finally dC = grad_out (P_T - dl / reg).  K and dC must be
+ * 16-byte aligned with ldk and lddc multiples of 4; m <= 8192.  The
+ * workspace (uot_backward_workspace_size bytes, 256-byte aligned) is
+ * caller-owned.  Asynchronous.
+ */
+size_t uot_backward_workspace_size(int64_t n, int64_t m);
+uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, int64_t ldc,
+                                 const float* a, const float* b, int64_t n, int64_t m, float reg,
+                                 float reg_m, int32_t iters, const void* hist, size_t hist_bytes,
+                                 double grad_out, float* dC, int64_t lddc, float* da, float* db,
+                                 void* workspace, size_t ws_bytes, void* stream);
+
 /* Synchronises `stream` and reads the result of the last uot_sinkhorn call
  * that used `workspace` (same n, m, opt).  Returns the device status as a
  * uot_status as uot_sinkhorn does with a non-NULL `out`. */

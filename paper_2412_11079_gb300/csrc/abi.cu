@@ -120,7 +120,8 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
                                int64_t n, int64_t m, float reg, float reg_m, int32_t iters,
                                double tol, float k_log2_scale, float* U, float* V,
                                void* workspace, size_t ws_bytes, const uot_options* opt,
-                               void* stream, uot_result* out) {
+                               void* stream, uot_result* out, void* hist = nullptr,
+                               size_t hist_bytes = 0) {
   const uot_options o = resolve(opt);
   if (!mat || !a || !b || !valid_dims(n, m) || ldm < m || !valid_dtype(o.dtype))
     return UOT_ERR_INVALID_ARG;
@@ -139,6 +140,10 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
   const WsLayout L = ws_layout(n, m);
   if (!workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(workspace) % 256)
     return UOT_ERR_WORKSPACE;
+  const HistLayout HL = hist_layout(n, m, iters);
+  if (hist && (!kf || hist_bytes < HL.total || reinterpret_cast<uintptr_t>(hist) % 256 ||
+               tol > 0.0))
+    return UOT_ERR_INVALID_ARG;
 
   const double fi_d = std::isinf(reg_m) ? 1.0 : double(reg_m) / (double(reg_m) + double(reg));
   const float fi = float(fi_d);
@@ -166,6 +171,10 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
   if (kf && launch_kform_reset(U, N, std::ldexp(1.0f, -int(std::lround(k_log2_scale))),
                                reinterpret_cast<float*>(ws + L.beta), M, int(L.mpad), a, b, fi,
                                reinterpret_cast<double*>(ws + L.log2k), s) != cudaSuccess)
+    return UOT_ERR_CUDA;
+  uint8_t* hb = static_cast<uint8_t*>(hist);
+  if (hist && launch_hist_init(hb, N, M, iters, std::ldexp(1.0f, -int(std::lround(k_log2_scale))),
+                               reinterpret_cast<const double*>(ws + L.log2k), s) != cudaSuccess)
     return UOT_ERR_CUDA;
   cudaEvent_t ev0 = static_cast<cudaEvent_t>(o.pass_events[0]);
   cudaEvent_t ev1 = static_cast<cudaEvent_t>(o.pass_events[1]);
@@ -225,6 +234,12 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
       A.ctr_clear = ctr + (t + 1) % 3;
       A.arrive = ctr + 3 + t % 3;
       A.arrive_clear = ctr + 3 + (t + 1) % 3;
+      if (hist) {
+        A.save_r = reinterpret_cast<float*>(hb + HL.r + size_t(t) * HL.strideU);
+        A.save_U = reinterpret_cast<float*>(hb + HL.U + size_t(t) * HL.strideU);
+        A.save_c = reinterpret_cast<float*>(hb + HL.c + size_t(t) * HL.strideV);
+        A.save_V = reinterpret_cast<float*>(hb + HL.V + size_t(t) * HL.strideV);
+      }
       if (fused_launch(kf, k, cs, grid, smem, tma, A, s) != cudaSuccess) return UOT_ERR_CUDA;
     }
     if (ev1 && cudaEventRecord(ev1, s) != cudaSuccess) return UOT_ERR_CUDA;
@@ -256,6 +271,16 @@ uot_status uot_sinkhorn_kform(const void* K, int64_t ldk, const float* a, const 
                               void* stream, uot_result* out) {
   return run_sinkhorn(true, const_cast<void*>(K), ldk, a, b, n, m, reg, reg_m, iters, tol,
                       k_log2_scale, U, V, workspace, ws_bytes, opt, stream, out);
+}
+
+uot_status uot_sinkhorn_kform_save(const void* K, int64_t ldk, const float* a, const float* b,
+                                   int64_t n, int64_t m, float reg, float reg_m, int32_t iters,
+                                   float k_log2_scale, float* U, float* V, void* hist,
+                                   size_t hist_bytes, void* workspace, size_t ws_bytes,
+                                   const uot_options* opt, void* stream, uot_result* out) {
+  if (!hist) return UOT_ERR_INVALID_ARG;
+  return run_sinkhorn(true, const_cast<void*>(K), ldk, a, b, n, m, reg, reg_m, iters, 0.0,
+                      k_log2_scale, U, V, workspace, ws_bytes, opt, stream, out, hist, hist_bytes);
 }
 
 uot_status uot_init_kernel_scaled(const float* C, int64_t ldc, void* K, int64_t ldk, int64_t n,

@@ -1,0 +1,575 @@
+// Adjoint of the unrolled Sinkhorn-UOT iteration (the rule of Section 2.1):
+// gradients of L = <P_T, C> with respect to C, a and b, from the history a
+// kernel-form forward solve saved (scalings U_t, V_t and sums r_t, c_t).
+//
+// In log space (l = -C/reg, f_t = log U_t, g_t = log V_t) the forward steps
+// are f_t = f_{t-1} + fi (log a - log r_t) and g_t = g_{t-1} + fi (log b -
+// log c_t) with r_t = rowsum(R_t), R_t = exp(l + f_{t-1} (+) g_{t-1}), and
+// c_t = colsum(Q_t), Q_t = exp(l + f_t (+) g_{t-1}).  Reverse mode from
+// dl = P_T * C, F = rowsum(dl), G = colsum(dl), for t = T .. 1:
+//   column step: w = -fi G / c_t, db += fi G / b, F += Q_t w,
+//                dl += Q_t * w, G = (1 - fi) G;
+//   row step:    z = -fi F / r_t, da += fi F / a, G += R_t^T z,
+//                dl += R_t * z, F = (1 - fi) F;
+// and dC = P_T - dl / reg.  Each reverse step is one sweep over the rows
+// with the same structure as the forward pass: Q_t and R_t are recomputed
+// per row from K and the saved scalings (never stored), the row reduction
+// (Q_t w)_i gives z_i, and R_t^T z is accumulated per column; dl is read and
+// written once per step (it lives in the dC buffer).  The last CTAs of a
+// step fold the column partials into G and prepare w for the next step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "uot_device.cuh"
+#include "uot_internal.h"
+
+namespace uot {
+
+namespace {
+
+constexpr int BW_BETA_CTAS = 16;
+
+struct BwArgs {
+  const float* K;
+  int64_t ldk;
+  float* D;  // dl, in the dC buffer
+  int64_t ldd;
+  int n, m, mpad;
+  const float* a;
+  const float* b;
+  float fi;
+  int t;           // reverse step (iteration index)
+  const double* log2k;  // gauge of the forward solve: Q_t = K U'_t V'_{t-1} 2^-e_t
+  const float* q;  // U'_t (n)
+  const float* pr; // U'_{t-1} (n)
+  const float* v;  // V'_{t-1} (mpad)
+  const float* r;  // r_t (n)
+  const float* c_prev;  // c_{t-1} (mpad), for the next step's w (t > 1)
+  float* F;        // row adjoints (n)
+  float* da;       // (n)
+  float* w;        // (mpad): w of this step, overwritten with the next step's
+  float* Gs;       // (mpad): (1 - fi) G entering this step's row part
+  float* db;       // (mpad)
+  float* h_next;   // (mpad) column partials R_t^T z, pre-zeroed
+  float* h_clear;  // buffer to clear for the next step
+  int* row_ctr;
+  int* ctr_clear;
+  int* arrive;
+  int* arrive_clear;
+  Control* ctl;
+  int stages;
+};
+
+template <int THREADS, int KV>
+__global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p) {
+  constexpr int VE = 4;
+  constexpr int NW = THREADS / 32;
+  constexpr int W = KV * VE * THREADS;
+  constexpr int ROW_BYTES = W * 4;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int stages = p.stages;
+  unsigned char* ring = smem;  // per slot: K row, then dl row
+  float* red = reinterpret_cast<float*>(smem + size_t(stages) * 2 * ROW_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(red + 2 * NW);
+  int* slot_row = reinterpret_cast<int*>(bars + stages);
+  __shared__ int s_arrival;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = p.n, m = p.m;
+  const double L2k = *p.log2k;
+  const float qscale =
+      ldexpf(1.0f, -int(rint(-double(p.t) * L2k) - rint(-double(p.t - 1) * L2k)));
+  const uint32_t copy_bytes = uint32_t((size_t(m) * 4) & ~size_t(15));
+  uint32_t st = 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  const uint64_t policy = policy_evict_first();
+  int issued = 0, next_row = n;
+  auto arm = [&](int q, int row) {
+    const int slot = q % stages;
+    if (row >= 0 && row < n) {
+      slot_row[slot] = row;
+      if (copy_bytes) {
+        mbar_arrive_expect_tx(&bars[slot], 2 * copy_bytes);
+        unsigned char* dst = ring + size_t(slot) * 2 * ROW_BYTES;
+        bulk_load(dst, p.K + int64_t(row) * p.ldk, copy_bytes, &bars[slot], policy);
+        bulk_load(dst + ROW_BYTES, p.D + int64_t(row) * p.ldd, copy_bytes, &bars[slot], policy);
+      } else {
+        mbar_arrive(&bars[slot]);
+      }
+    } else {
+      slot_row[slot] = -1;
+      mbar_arrive(&bars[slot]);
+    }
+  };
+  if (tid == 0) {
+    const int base = atomicAdd(p.row_ctr, stages);
+    for (int q = 0; q < stages; ++q) arm(q, base + q);
+    issued = stages;
+    if (base + stages < n) next_row = atomicAdd(p.row_ctr, 1);
+  }
+
+  // This step's column values: V'_{t-1} and w.
+  float v[KV][VE], w[KV][VE], h[KV][VE];
+#pragma unroll
+  for (int k = 0; k < KV; ++k) {
+    const int cc = (k * THREADS + tid) * VE;
+#pragma unroll
+    for (int e = 0; e < VE; ++e) {
+      v[k][e] = cc + e < m ? __ldcg(p.v + cc + e) : 0.0f;
+      w[k][e] = cc + e < m ? __ldcg(p.w + cc + e) : 0.0f;
+      h[k][e] = 0.0f;
+    }
+  }
+  {
+    const int g = blockIdx.x * THREADS + tid, gs = gridDim.x * THREADS;
+    for (int j = g; j < p.mpad; j += gs) p.h_clear[j] = 0.0f;
+    if (blockIdx.x == 0 && tid == 0) {
+      *p.ctr_clear = 0;
+      *p.arrive_clear = 0;
+    }
+  }
+
+  bool broken = false;
+  int done_rows = 0;
+  for (int q = 0;; ++q) {
+    const int slot = q % stages;
+    if (!broken && !mbar_wait_bounded(&bars[slot], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS)) {
+      broken = true;
+      st |= DEV_TIMEOUT;
+    }
+    const int row = *reinterpret_cast<volatile int*>(&slot_row[slot]);
+    if (row < 0 || row >= n) break;
+    const float qi = __ldcg(p.q + row) * qscale;
+    const float pi = __ldcg(p.pr + row);
+    const float ri = __ldcg(p.r + row);
+    const float ai = __ldg(p.a + row);
+    const float Fi = __ldcg(p.F + row);
+    const unsigned char* sK = ring + size_t(slot) * 2 * ROW_BYTES;
+    const unsigned char* sD = sK + ROW_BYTES;
+    const float* gK = p.K + int64_t(row) * p.ldk;
+    float* gD = p.D + int64_t(row) * p.ldd;
+    float x[KV][VE], d[KV][VE];
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      const int li = k * THREADS + tid;
+      const int cc = li * VE;
+      if (cc + VE <= m) {
+        Elem<float>::unpack(ld_shared_v4(sK + size_t(li) * 16), x[k]);
+        Elem<float>::unpack(ld_shared_v4(sD + size_t(li) * 16), d[k]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VE; ++e) {
+          x[k][e] = cc + e < m ? gK[cc + e] : 0.0f;
+          d[k][e] = cc + e < m ? gD[cc + e] : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < VE; ++e) s = fmaf(x[k][e] * v[k][e], w[k][e], s);
+    }
+    s = warp_sum(s);
+    float* rb = red + (q & 1) * NW;
+    if (lane == 0) rb[warp] = s;
+    if (__syncthreads_or(broken ? 1 : 0)) {
+      broken = true;
+      st |= DEV_TIMEOUT;
+      break;
+    }
+    if (tid == 0 && !broken) {
+      const int r2 = next_row;
+      arm(issued, r2);
+      ++issued;
+      if (r2 < n) next_row = atomicAdd(p.row_ctr, 1);
+    }
+    float S1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) S1 += rb[k];
+    // Column step: F += (Q_t w)_i; row step: z, da, F.
+    const float Fn = Fi + qi * S1;
+    const float z = -p.fi * Fn / ri;
+    if (tid == 0) {
+      p.da[row] += p.fi * Fn / ai;
+      p.F[row] = (1.0f - p.fi) * Fn;
+    }
+    const float pz = pi * z;
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      const int cc = (k * THREADS + tid) * VE;
+      float y[VE];
+#pragma unroll
+      for (int e = 0; e < VE; ++e) {
+        const float kv = x[k][e] * v[k][e];
+        h[k][e] = fmaf(kv, pz, h[k][e]);
+        y[e] = fmaf(kv, fmaf(qi, w[k][e], pz), d[k][e]);
+      }
+      if (cc + VE <= m) {
+        st_global_cs_v4(gD + cc, Elem<float>::pack(y));
+      } else {
+#pragma unroll
+        for (int e = 0; e < VE; ++e)
+          if (cc + e < m) gD[cc + e] = y[e];
+      }
+    }
+    ++done_rows;
+  }
+  if (done_rows > 0) {
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      const int cc = (k * THREADS + tid) * VE;
+      if (cc + VE <= m) {
+        red_add_v4(p.h_next + cc, h[k][0], h[k][1], h[k][2], h[k][3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VE; ++e)
+          if (cc + e < m) atomicAdd(p.h_next + cc + e, h[k][e]);
+      }
+    }
+  }
+  if (st) atomicOr(&p.ctl->status, st);
+  // The last CTAs: G = (1 - fi) G_prev + R_t^T z; db and the next step's w.
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_arrival = atomicAdd(p.arrive, 1);
+  }
+  __syncthreads();
+  const int G = int(gridDim.x);
+  const int K = min(G, BW_BETA_CTAS);
+  const int slice = s_arrival - (G - K);
+  if (slice >= 0) {
+    if (tid == 0) {
+      const uint64_t t0 = global_timer_ns();
+      while (ld_acquire_gpu(p.arrive) < G) {
+        if (global_timer_ns() - t0 > WAIT_LIMIT_NS) {
+          atomicOr(&p.ctl->status, DEV_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    const int per = (m + K - 1) / K;
+    const int j0 = slice * per, j1 = min(m, j0 + per);
+    for (int j = j0 + tid; j < j1; j += THREADS) {
+      const float Gj = p.Gs[j] + __ldcg(p.h_next + j);
+      if (p.t > 1) {
+        p.db[j] += p.fi * Gj / __ldg(p.b + j);
+        p.w[j] = -p.fi * Gj / __ldcg(p.c_prev + j);
+        p.Gs[j] = (1.0f - p.fi) * Gj;
+      }
+    }
+  }
+  if (tid == 0 && broken) {
+    for (int q = max(0, issued - stages); q < issued; ++q)
+      mbar_wait_bounded(&bars[q % stages], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS);
+  }
+}
+
+constexpr int TB = 256;
+
+// dl = P_T * C with P_T = (U_i K_ij) V_j; F = rowsum(dl) (one warp per row).
+__global__ void __launch_bounds__(TB) bw_init_kernel(const float* K, int64_t ldk, const float* C,
+                                                     int64_t ldc, const float* U, const float* V,
+                                                     float* D, int64_t ldd, int n, int m,
+                                                     float* F, float* da) {
+  const int warp = (blockIdx.x * TB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * TB) >> 5;
+  for (int i = warp; i < n; i += nw) {
+    float s = 0.0f;
+    const float u = U[i];
+    for (int j = lane; j < m; j += 32) {
+      const float dl = (u * K[int64_t(i) * ldk + j]) * V[j] * C[int64_t(i) * ldc + j];
+      D[int64_t(i) * ldd + j] = dl;
+      s += dl;
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      F[i] = s;
+      da[i] = 0.0f;
+    }
+  }
+}
+
+// G0 = colsum(dl): a column per thread over a stride of rows, then atomics.
+__global__ void __launch_bounds__(TB) bw_colsum_kernel(const float* D, int64_t ldd, int n, int m,
+                                                       float* G0) {
+  const int j = blockIdx.x * TB + threadIdx.x;
+  if (j >= m) return;
+  float s = 0.0f;
+  for (int i = blockIdx.y; i < n; i += gridDim.y) s += D[int64_t(i) * ldd + j];
+  atomicAdd(G0 + j, s);
+}
+
+// w_T = -fi G0 / c_T, db = fi G0 / b, Gs = (1 - fi) G0.
+__global__ void bw_cols_kernel(const float* G0, const float* cT, const float* b, float fi, int m,
+                               float* w, float* db, float* Gs) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const float G = G0[j];
+  w[j] = -fi * G / cT[j];
+  db[j] = fi * G / b[j];
+  Gs[j] = (1.0f - fi) * G;
+}
+
+// dC = g (P_T - dl / reg), da *= g, db *= g.
+__global__ void __launch_bounds__(TB) bw_final_kernel(const float* K, int64_t ldk, const float* U,
+                                                      const float* V, float* D, int64_t ldd,
+                                                      int n, int m, float inv_reg, float g,
+                                                      float* da, float* db) {
+  const int j = blockIdx.x * TB + threadIdx.x;
+  if (blockIdx.y == 0) {
+    for (int i = j; i < n; i += gridDim.x * TB) da[i] *= g;
+    if (j < m) db[j] *= g;
+  }
+  if (j >= m) return;
+  const float v = V[j];
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    const float P = (U[i] * K[int64_t(i) * ldk + j]) * v;
+    float* dp = D + int64_t(i) * ldd + j;
+    *dp = g * (P - *dp * inv_reg);
+  }
+}
+
+__global__ void bw_hist_init_kernel(uint8_t* hist, HistLayout L, int n, int m, int iters,
+                                    float u0, const double* log2k) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gs = gridDim.x * blockDim.x;
+  float* U0 = reinterpret_cast<float*>(hist + L.U);
+  float* V0 = reinterpret_cast<float*>(hist + L.V);
+  for (int i = g; i < n; i += gs) U0[i] = u0;
+  for (int j = g; j < m; j += gs) V0[j] = 1.0f;
+  if (g == 0) {
+    HistHeader* H = reinterpret_cast<HistHeader*>(hist);
+    H->log2k = *log2k;
+    H->n = n;
+    H->m = m;
+    H->iters = iters;
+    H->k_scale_inv = u0;
+  }
+}
+
+struct BwEntry {
+  int threads, kv;
+  const void* fn;
+};
+#define BW_ENTRY(TH, KV) \
+  BwEntry { TH, KV, reinterpret_cast<const void*>(&reverse_pass_kernel<TH, KV>) }
+const BwEntry kBw[] = {BW_ENTRY(512, 4), BW_ENTRY(256, 4), BW_ENTRY(128, 4),
+                       BW_ENTRY(128, 2), BW_ENTRY(64, 2),  BW_ENTRY(32, 2)};
+constexpr int kBwNum = int(sizeof(kBw) / sizeof(kBw[0]));
+
+size_t bw_smem(const BwEntry& e, int stages) {
+  const size_t row = size_t(e.threads) * e.kv * 16;
+  return size_t(stages) * 2 * row + 2 * (e.threads / 32) * 4 + size_t(stages) * 12;
+}
+
+struct BwLayout {
+  size_t ctl, F, da, w, Gs, G0, h[3], ctr, total;
+};
+BwLayout bw_layout(int64_t n, int64_t m) {
+  BwLayout L{};
+  const size_t npad = size_t((n + 63) & ~int64_t(63)) * 4, mpad = size_t((m + 63) & ~int64_t(63)) * 4;
+  size_t off = 0;
+  L.ctl = off; off = align256(off + sizeof(Control));
+  L.F = off; off = align256(off + npad);
+  L.da = off; off = align256(off + npad);
+  L.w = off; off = align256(off + mpad);
+  L.Gs = off; off = align256(off + mpad);
+  L.G0 = off; off = align256(off + mpad);
+  for (int k = 0; k < 3; ++k) { L.h[k] = off; off = align256(off + mpad); }
+  L.ctr = off; off = align256(off + 6 * sizeof(int));
+  L.total = off;
+  return L;
+}
+
+std::mutex g_bw_mu;
+size_t g_bw_smem_set[64][kBwNum];
+
+}  // namespace
+
+cudaError_t launch_hist_init(uint8_t* hist, int n, int m, int iters, float u0, const double* log2k,
+                             cudaStream_t s) {
+  const HistLayout L = hist_layout(n, m, iters);
+  bw_hist_init_kernel<<<(std::max(n, m) + 255) / 256, 256, 0, s>>>(hist, L, n, m, iters, u0, log2k);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
+}  // namespace uot
+
+using namespace uot;
+
+extern "C" {
+
+size_t uot_grad_hist_size(int64_t n, int64_t m, int32_t iters) {
+  if (n < 1 || m < 1 || iters < 0 || n > INT32_MAX || m > INT32_MAX / 2) return 0;
+  return hist_layout(n, m, iters).total;
+}
+
+size_t uot_backward_workspace_size(int64_t n, int64_t m) {
+  if (n < 1 || m < 1 || n > INT32_MAX || m > INT32_MAX / 2) return 0;
+  return bw_layout(n, m).total;
+}
+
+uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, int64_t ldc,
+                                 const float* a, const float* b, int64_t n, int64_t m, float reg,
+                                 float reg_m, int32_t iters, const void* hist, size_t hist_bytes,
+                                 double grad_out, float* dC, int64_t lddc, float* da, float* db,
+                                 void* workspace, size_t ws_bytes, void* stream) {
+  if (!K || !C || !a || !b || !hist || !dC || !da || !db || n < 1 || m < 1 || n > INT32_MAX ||
+      m > INT32_MAX / 2 || ldk < m || ldc < m || lddc < m)
+    return UOT_ERR_INVALID_ARG;
+  if (!(reg > 0.0f) || !std::isfinite(reg) || !(reg_m > 0.0f) || !std::isfinite(grad_out))
+    return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(K) % 16 || reinterpret_cast<uintptr_t>(dC) % 16 ||
+      ldk % 4 || lddc % 4)
+    return UOT_ERR_INVALID_ARG;  // rows of K and dC are fetched with bulk copies
+  if (iters < 0) return UOT_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int T = iters, N = int(n), M = int(m);
+  const HistLayout HL = hist_layout(n, m, T);
+  if (hist_bytes < HL.total) return UOT_ERR_INVALID_ARG;
+  const BwLayout L = bw_layout(n, m);
+  if (!workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(workspace) % 256)
+    return UOT_ERR_WORKSPACE;
+  int k = -1;
+  for (int i = 0; i < kBwNum; ++i)
+    if (kBw[i].threads * kBw[i].kv * 4 >= M && (k < 0 || kBw[i].threads * kBw[i].kv < kBw[k].threads * kBw[k].kv))
+      k = i;
+  if (k < 0) return UOT_ERR_UNSUPPORTED;  // rows wider than one CTA (8192 columns)
+
+  const double fi_d = std::isinf(reg_m) ? 1.0 : double(reg_m) / (double(reg_m) + double(reg));
+  const float fi = float(fi_d);
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  const uint8_t* hb = static_cast<const uint8_t*>(hist);
+  auto U_t = [&](int t) { return reinterpret_cast<const float*>(hb + HL.U + size_t(t) * HL.strideU); };
+  auto V_t = [&](int t) { return reinterpret_cast<const float*>(hb + HL.V + size_t(t) * HL.strideV); };
+  auto r_t = [&](int t) { return reinterpret_cast<const float*>(hb + HL.r + size_t(t) * HL.strideU); };
+  auto c_t = [&](int t) { return reinterpret_cast<const float*>(hb + HL.c + size_t(t) * HL.strideV); };
+  float* F = reinterpret_cast<float*>(ws + L.F);
+  float* w = reinterpret_cast<float*>(ws + L.w);
+  float* Gs = reinterpret_cast<float*>(ws + L.Gs);
+  float* G0 = reinterpret_cast<float*>(ws + L.G0);
+  int* ctr = reinterpret_cast<int*>(ws + L.ctr);
+  Control* ctl = reinterpret_cast<Control*>(ws + L.ctl);
+
+  if (cudaMemsetAsync(ws, 0, L.total, s) != cudaSuccess) return UOT_ERR_CUDA;
+  {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    bw_init_kernel<<<sms * 8, TB, 0, s>>>(K, ldk, C, ldc, U_t(T), V_t(T), dC, lddc, N, M, F, da);
+    if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
+    count_launch();
+    const int gx = (M + TB - 1) / TB;
+    const int gy = std::max(1, std::min(std::min(N, 65535), (sms * 8 + gx - 1) / gx));
+    bw_colsum_kernel<<<dim3(gx, gy), TB, 0, s>>>(dC, lddc, N, M, G0);
+    if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
+    count_launch();
+  }
+  if (T > 0) {
+    bw_cols_kernel<<<(M + 255) / 256, 256, 0, s>>>(G0, c_t(T), b, fi, M, w, db, Gs);
+    if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
+    count_launch();
+  } else {
+    if (cudaMemsetAsync(db, 0, size_t(M) * 4, s) != cudaSuccess) return UOT_ERR_CUDA;
+  }
+
+  // Geometry of the reverse pass.
+  const BwEntry& e = kBw[k];
+  int dev = 0, sms = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return UOT_ERR_CUDA;
+  int stages = 2, occ = 0;
+  for (int st = 8; st >= 2; --st)
+    if (bw_smem(e, st) <= size_t(optin)) {
+      stages = st;
+      break;
+    }
+  // Prefer more CTAs per SM over a deeper ring once two slots fit.
+  int best_occ = 0, best_st = stages;
+  for (int st = 2; st <= stages; ++st) {
+    const size_t b2 = bw_smem(e, st);
+    {
+      std::lock_guard<std::mutex> lock(g_bw_mu);
+      if (dev < 64 && g_bw_smem_set[dev][k] < b2) {
+        if (cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b2)) !=
+            cudaSuccess)
+          return UOT_ERR_CUDA;
+        g_bw_smem_set[dev][k] = b2;
+      }
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e.fn, e.threads, b2) != cudaSuccess)
+      return UOT_ERR_CUDA;
+    if (occ == 0) break;
+    if (st == 2) best_occ = occ;
+    if (occ < best_occ) break;
+    best_st = st;
+  }
+  if (best_occ == 0) return UOT_ERR_CUDA;
+  const size_t smem = bw_smem(e, best_st);
+  int grid = best_occ * sms;
+  if (grid > (N + 1) / 2) grid = std::max(1, (N + 1) / 2);
+
+  BwArgs A{};
+  A.K = K;
+  A.ldk = ldk;
+  A.D = dC;
+  A.ldd = lddc;
+  A.n = N;
+  A.m = M;
+  A.mpad = int((m + 63) & ~int64_t(63));
+  A.a = a;
+  A.b = b;
+  A.fi = fi;
+  A.F = F;
+  A.da = da;
+  A.w = w;
+  A.Gs = Gs;
+  A.db = db;
+  A.ctl = ctl;
+  A.stages = best_st;
+  for (int t = T; t >= 1; --t) {
+    const int q = T - t;  // pass counter for the rings
+    A.t = t;
+    A.log2k = reinterpret_cast<const double*>(hb);  // HistHeader::log2k
+    A.q = U_t(t);
+    A.pr = U_t(t - 1);
+    A.v = V_t(t - 1);
+    A.r = r_t(t);
+    A.c_prev = t > 1 ? c_t(t - 1) : c_t(t);
+    A.h_next = reinterpret_cast<float*>(ws + L.h[q % 3]);
+    A.h_clear = reinterpret_cast<float*>(ws + L.h[(q + 1) % 3]);
+    A.row_ctr = ctr + q % 3;
+    A.ctr_clear = ctr + (q + 1) % 3;
+    A.arrive = ctr + 3 + q % 3;
+    A.arrive_clear = ctr + 3 + (q + 1) % 3;
+    void* kargs[] = {&A};
+    if (cudaLaunchKernel(e.fn, dim3(grid), dim3(e.threads), kargs, smem, s) != cudaSuccess)
+      return UOT_ERR_CUDA;
+    count_launch();
+  }
+  {
+    const int gx = (M + TB - 1) / TB;
+    int gy = (sms * 8 + gx - 1) / gx;
+    gy = std::max(1, std::min(gy, std::min(N, 65535)));
+    bw_final_kernel<<<dim3(gx, gy), TB, 0, s>>>(K, ldk, U_t(T), V_t(T), dC, lddc, N, M, 1.0f / reg,
+                                              float(grad_out), da, db);
+    if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
+    count_launch();
+  }
+  return UOT_OK;
+}
+
+}  // extern "C"

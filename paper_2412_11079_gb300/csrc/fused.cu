@@ -152,7 +152,9 @@ cudaError_t fused_geometry(bool kf, int k, int cs, int n, int* grid, int* stages
     if (nc <= 0) return cudaErrorInvalidConfiguration;
     clusters = nc;
   }
-  // Keep at least two rows per cluster so the column flush stays small.
+  // Keep at least two rows per cluster so the column flush stays small
+  // (fewer, longer-lived CTAs measured slower for short rows: with one row in
+  // flight per CTA, more CTAs per SM hide the per-row latency).
   const int cap = (n + 1) / 2;
   if (clusters > cap) clusters = cap > 0 ? cap : 1;
   *grid = clusters * cs;

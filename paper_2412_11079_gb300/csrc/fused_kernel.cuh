@@ -326,7 +326,13 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
       // (the column sums are V_j 2^-e_t times these).
       tot *= u_old;
       const float u_new = u_old * rescale_factor(arow, tot, p.fi, st) * gauge;
-      if (cr == 0 && tid == 0) p.U[row] = u_new;
+      if (cr == 0 && tid == 0) {
+        p.U[row] = u_new;
+        if (p.save_r) {  // history for the adjoint: r_t and U_t of this row
+          p.save_r[row] = tot;
+          p.save_U[row] = u_new;
+        }
+      }
 #pragma unroll
       for (int k = 0; k < KV; ++k)
 #pragma unroll
@@ -416,7 +422,12 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
         // V_j <- V_j (b_j / c_j)^fi 2^-e_t with c_j = V_j 2^-e_t sum_i U_i K_ij.
         const float v = __ldcg(p.beta_out + j);
         const float c = v * __ldcg(p.c_next + j) * inv_gauge;
-        p.beta_out[j] = v * rescale_factor(__ldg(p.b_ws + j), c, p.fi, st2) * inv_gauge;
+        const float v_new = v * rescale_factor(__ldg(p.b_ws + j), c, p.fi, st2) * inv_gauge;
+        p.beta_out[j] = v_new;
+        if (p.save_c) {  // history for the adjoint: c_t and V_t of this column
+          p.save_c[j] = c;
+          p.save_V[j] = v_new;
+        }
       } else {
         p.beta_out[j] = rescale_factor(__ldg(p.b_ws + j), __ldcg(p.c_next + j), p.fi, st2);
       }

@@ -97,7 +97,38 @@ struct FusedArgs {
   const double* log2k; // kernel form: log2 k for the power-of-two gauge
   const float* beta;   // beta_{t-1}, zero-padded to mpad (read unless first)
   float* beta_out;     // beta_t, written by the last CTAs of this pass
+  float* save_r;       // kernel form, optional: r_t (n) of this iteration
+  float* save_U;       // U_t (n)
+  float* save_c;       // c_t (m)
+  float* save_V;       // V_t (m)
 };
+
+// History of a kernel-form solve kept for the adjoint: a header, then for
+// t = 0..iters the scalings U_t (npad floats), V_t (mpad), row sums r_t (npad)
+// and column sums c_t (mpad); entries t = 0 of r and c are unused.
+struct HistHeader {
+  double log2k;
+  int32_t n, m, iters;
+  float k_scale_inv;
+};
+struct HistLayout {
+  size_t U, V, r, c, total;  // offsets of the t = 0 arrays
+  size_t strideU, strideV;   // bytes per iteration
+};
+inline HistLayout hist_layout(int64_t n, int64_t m, int iters) {
+  HistLayout L{};
+  const int64_t npad = (n + 63) & ~int64_t(63), mpad = (m + 63) & ~int64_t(63);
+  const size_t T1 = size_t(iters) + 1;
+  L.strideU = size_t(npad) * 4;
+  L.strideV = size_t(mpad) * 4;
+  size_t off = align256(sizeof(HistHeader));
+  L.U = off; off += T1 * L.strideU;
+  L.V = off; off += T1 * L.strideV;
+  L.r = off; off += T1 * L.strideU;
+  L.c = off; off += T1 * L.strideV;
+  L.total = align256(off);
+  return L;
+}
 
 struct FusedConfig {
   int dtype;
@@ -140,6 +171,9 @@ cudaError_t launch_reset(uint8_t* ws, WsLayout L, const float* b, int m, cudaStr
 cudaError_t launch_multipass_iter(void* P, int64_t ldp, int n, int m, int dtype, const float* a,
                                   const float* b, float fi, int t, double tol, int check_every,
                                   uint8_t* ws, WsLayout L, cudaStream_t s, int* launches);
+
+cudaError_t launch_hist_init(uint8_t* hist, int n, int m, int iters, float u0, const double* log2k,
+                             cudaStream_t s);
 
 void count_launch(int k = 1);
 

@@ -84,6 +84,14 @@ SIGNATURES = {
                                           ctypes.POINTER(UotResult)]),
     "uot_kform_plan": (ctypes.c_int, [_P, _I64, _I32, _P, _P, _I64, _I64, _P, _I64, _I32, _P]),
     "uot_kform_cost": (ctypes.c_int, [_P, _I64, _I32, _P, _P, _P, _I64, _I64, _I64, _P, _P]),
+    "uot_grad_hist_size": (_SZ, [_I64, _I64, _I32]),
+    "uot_sinkhorn_kform_save": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _F,
+                                               _P, _P, _P, _SZ, _P, _SZ,
+                                               ctypes.POINTER(UotOptions), _P,
+                                               ctypes.POINTER(UotResult)]),
+    "uot_backward_workspace_size": (_SZ, [_I64, _I64]),
+    "uot_sinkhorn_backward": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _P, _I64, _I64, _F, _F,
+                                             _I32, _P, _SZ, _D, _P, _I64, _P, _P, _P, _SZ, _P]),
     "uot_sinkhorn_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _D,
                                             ctypes.POINTER(UotOptions), _P,
                                             ctypes.POINTER(UotResult)]),
@@ -424,3 +432,50 @@ def uot_batched_results(ws, nprob: int, stream=None, check_status: bool = True):
             check_status and st != UOT_OK):
         raise UotError(st, "uot_batched_results")
     return [SinkhornResult(r.iters_done, r.dev_status, r.err) for r in out]
+
+
+def uot_sinkhorn_kform_save(K, a, b, reg: float, reg_m: float, iters: int, U=None, V=None,
+                            hist=None, ws=None, stream=None):
+    """Kernel-form solve of exactly `iters` iterations that keeps the history
+    its adjoint needs; returns (U, V, hist)."""
+    torch = _torch()
+    n, m = K.shape
+    if K.dtype != torch.float32:
+        raise ValueError("the differentiable solve keeps K in FP32")
+    U = torch.empty(n, device=K.device) if U is None else U
+    V = torch.empty(m, device=K.device) if V is None else V
+    if hist is None:
+        hist = workspace_bytes(int(load().uot_grad_hist_size(n, m, iters)), K.device)
+    if ws is None:
+        ws = workspace(n, m, None, K.device)
+    kp, ldk = _matrix(K, "K")
+    res = UotResult()
+    _check(load().uot_sinkhorn_kform_save(kp, ldk, _vector(a, "a", n), _vector(b, "b", m), n, m,
+                                          float(reg), float(reg_m), int(iters), 0.0,
+                                          _vector(U, "U", n), _vector(V, "V", m),
+                                          hist.data_ptr(), hist.numel(), ws.data_ptr(),
+                                          ws.numel(), None, _stream(stream), None),
+           "uot_sinkhorn_kform_save")
+    return U, V, hist
+
+
+def uot_sinkhorn_backward(K, C, a, b, reg: float, reg_m: float, iters: int, hist,
+                          grad_out: float = 1.0, dC=None, da=None, db=None, ws=None,
+                          stream=None):
+    torch = _torch()
+    n, m = K.shape
+    dC = torch.empty((n, (m + 3) // 4 * 4), device=K.device)[:, :m] if dC is None else dC
+    da = torch.empty(n, device=K.device) if da is None else da
+    db = torch.empty(m, device=K.device) if db is None else db
+    if ws is None:
+        ws = workspace_bytes(int(load().uot_backward_workspace_size(n, m)), K.device)
+    kp, ldk = _matrix(K, "K")
+    cp, ldc = _matrix(C, "C")
+    gp, ldd = _matrix(dC, "dC")
+    _check(load().uot_sinkhorn_backward(kp, ldk, cp, ldc, _vector(a, "a", n), _vector(b, "b", m),
+                                        n, m, float(reg), float(reg_m), int(iters),
+                                        hist.data_ptr(), hist.numel(), float(grad_out), gp, ldd,
+                                        _vector(da, "da", n), _vector(db, "db", m),
+                                        ws.data_ptr(), ws.numel(), _stream(stream)),
+           "uot_sinkhorn_backward")
+    return dC, da, db
