@@ -357,14 +357,24 @@ def run_grad(args):
         bufs.append((p, C, a, b, K, U, V, hist, ws, bws, dC, da, db, cost))
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
+    # The problems run as parallel branches (one stream each), every launch
+    # limited to a share of the GPU, so the fixed cost of each 16 MB pass
+    # overlaps with the other problems' passes.
+    branches = [torch.cuda.Stream() for _ in range(min(args.grad_streams, len(bufs)))]
+    opt = uot.options(max_ctas=args.grad_max_ctas)
 
     def step(s):
-        for (p, C, a, b, K, U, V, hist, ws, bws, dC, da, db, cost) in bufs:
-            uot.uot_init_kernel(C, K, p.reg, stream=s)
-            uot.uot_sinkhorn_kform_save(K, a, b, p.reg, p.reg_m, iters, U, V, hist, ws, s)
-            uot.uot_kform_cost(K, U, V, C, cost, s)
+        for br in branches:
+            br.wait_stream(s)
+        for i, (p, C, a, b, K, U, V, hist, ws, bws, dC, da, db, cost) in enumerate(bufs):
+            bs = branches[i % len(branches)]
+            uot.uot_init_kernel(C, K, p.reg, stream=bs)
+            uot.uot_sinkhorn_kform_save(K, a, b, p.reg, p.reg_m, iters, U, V, hist, ws, bs, opt)
+            uot.uot_kform_cost(K, U, V, C, cost, bs)
             uot.uot_sinkhorn_backward(K, C, a, b, p.reg, p.reg_m, iters, hist, 1.0, dC, da, db,
-                                      bws, s)
+                                      bws, bs, opt)
+        for br in branches:
+            s.wait_stream(br)
 
     g = torch.cuda.CUDAGraph()
     with torch.cuda.stream(stream):
@@ -398,9 +408,14 @@ def run_grad(args):
         return float(np.max(np.abs(x.double().cpu().numpy() - r)) / np.max(np.abs(r)))
     # forward-only timing of the same batch
     def fwd(s):
-        for (p, C, a, b, K, U, V, hist, ws, bws, dC, da, db, cost) in bufs:
-            uot.uot_init_kernel(C, K, p.reg, stream=s)
-            uot.uot_sinkhorn_kform_save(K, a, b, p.reg, p.reg_m, iters, U, V, hist, ws, s)
+        for br in branches:
+            br.wait_stream(s)
+        for i, (p, C, a, b, K, U, V, hist, ws, bws, dC, da, db, cost) in enumerate(bufs):
+            bs = branches[i % len(branches)]
+            uot.uot_init_kernel(C, K, p.reg, stream=bs)
+            uot.uot_sinkhorn_kform_save(K, a, b, p.reg, p.reg_m, iters, U, V, hist, ws, bs, opt)
+        for br in branches:
+            s.wait_stream(br)
     with torch.cuda.stream(stream):
         fwd(stream)
         torch.cuda.synchronize()
@@ -413,6 +428,7 @@ def run_grad(args):
         "workload": f"grad: {len(probs)} problems N=M={n}, {iters} iterations, forward + adjoint",
         "unit": UNIT, "ms_per_step": ms, "elems_per_s": elems / (ms * 1e-3),
         "forward_ms": fwd_ms, "backward_ms": ms - fwd_ms,
+        "branches": len(branches), "max_ctas_per_launch": args.grad_max_ctas,
         "alg_gbs": (elems * (4.0 + 12.0)) / (ms * 1e-3) / 1e9,
         "grad_rel_err": {"iters": q.iters, "dC": rel(Cq.grad, rdC), "da": rel(aq.grad, rda),
                          "db": rel(bq.grad, rdb)},
@@ -444,6 +460,8 @@ def main():
                     choices=["large", "precision", "batched", "grad"])
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--grad-check-iters", type=int, default=5)
+    ap.add_argument("--grad-streams", type=int, default=8)
+    ap.add_argument("--grad-max-ctas", type=int, default=80)
     ap.add_argument("--acc-n", type=int, default=8192)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

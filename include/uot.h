@@ -71,7 +71,10 @@ typedef struct uot_options {
   int32_t tile;         /* 0 = automatic; k > 0 forces fused config k-1 of
                            uot_fused_config() (for tuning and tests)          */
   int32_t cluster;      /* 0 = automatic; else CTAs per row (1..8), fused only */
-  int32_t reserved[3];  /* must be 0                                          */
+  int32_t max_ctas;     /* 0 = as many CTAs as fit; else at most this many per
+                           launch (to run several solves side by side, e.g.
+                           as parallel branches of one CUDA graph)          */
+  int32_t reserved[2];  /* must be 0                                          */
   void* pass_events[2]; /* optional cudaEvent_t pair: uot_sinkhorn records
                            [0] on `stream` just before its first iteration
                            pass and [1] just after its last (NULL = none);
@@ -228,14 +231,15 @@ uot_status uot_sinkhorn_kform_save(const void* K, int64_t ldk, const float* a, c
  * dl = P_T * C; finally dC = grad_out (P_T - dl / reg).  K and dC must be
  * 16-byte aligned with ldk and lddc multiples of 4; m <= 8192.  The
  * workspace (uot_backward_workspace_size bytes, 256-byte aligned) is
- * caller-owned.  Asynchronous.
+ * caller-owned.  opt may be NULL; only opt->max_ctas is used.  Asynchronous.
  */
 size_t uot_backward_workspace_size(int64_t n, int64_t m);
 uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, int64_t ldc,
                                  const float* a, const float* b, int64_t n, int64_t m, float reg,
                                  float reg_m, int32_t iters, const void* hist, size_t hist_bytes,
                                  double grad_out, float* dC, int64_t lddc, float* da, float* db,
-                                 void* workspace, size_t ws_bytes, void* stream);
+                                 void* workspace, size_t ws_bytes, const uot_options* opt,
+                                 void* stream);
 
 /* Synchronises `stream` and reads the result of the last uot_sinkhorn call
  * that used `workspace` (same n, m, opt).  Returns the device status as a

@@ -1,6 +1,7 @@
 // The extern "C" entry points of libuot (declared in include/uot.h): argument
 // validation on the host, workspace layout, and the per-iteration launch
 // sequence of the Sinkhorn-UOT iteration (Section 2.1 / Algorithm 1).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -31,7 +32,7 @@ static uot_options resolve(const uot_options* opt) {
 }
 
 static bool reserved_zero(const uot_options& o) {
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 2; ++k)
     if (o.reserved[k] != 0) return false;
   return true;
 }
@@ -129,7 +130,7 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
     return UOT_ERR_INVALID_ARG;
   if (std::isnan(tol) || std::isinf(tol) || !reserved_zero(o)) return UOT_ERR_INVALID_ARG;
   if (o.algo != UOT_ALGO_FUSED && o.algo != UOT_ALGO_MULTIPASS) return UOT_ERR_INVALID_ARG;
-  if (o.cluster < 0 || o.cluster > 8 || o.tile < 0) return UOT_ERR_INVALID_ARG;
+  if (o.cluster < 0 || o.cluster > 8 || o.tile < 0 || o.max_ctas < 0) return UOT_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(mat) % esize(o.dtype) ||
       reinterpret_cast<uintptr_t>(a) % 4 || reinterpret_cast<uintptr_t>(b) % 4)
     return UOT_ERR_INVALID_ARG;
@@ -165,6 +166,7 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
     if (cs > 8) return UOT_ERR_UNSUPPORTED;
     if (int64_t(cs) * cfg.cols < m) return UOT_ERR_INVALID_ARG;
     if (fused_geometry(kf, k, cs, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
+    if (o.max_ctas > 0 && grid > o.max_ctas) grid = std::max(cs, (o.max_ctas / cs) * cs);
   }
 
   if (launch_reset(ws, L, b, M, s) != cudaSuccess) return UOT_ERR_CUDA;
@@ -234,6 +236,8 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
       A.ctr_clear = ctr + (t + 1) % 3;
       A.arrive = ctr + 3 + t % 3;
       A.arrive_clear = ctr + 3 + (t + 1) % 3;
+      A.slice_ctr = ctr + 6 + t % 3;
+      A.slice_clear = ctr + 6 + (t + 1) % 3;
       if (hist) {
         A.save_r = reinterpret_cast<float*>(hb + HL.r + size_t(t) * HL.strideU);
         A.save_U = reinterpret_cast<float*>(hb + HL.U + size_t(t) * HL.strideU);

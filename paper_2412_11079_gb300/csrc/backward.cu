@@ -59,6 +59,8 @@ struct BwArgs {
   int* ctr_clear;
   int* arrive;
   int* arrive_clear;
+  int* slice_ctr;
+  int* slice_clear;
   Control* ctl;
   int stages;
 };
@@ -75,7 +77,6 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
   float* red = reinterpret_cast<float*>(smem + size_t(stages) * 2 * ROW_BYTES);
   uint64_t* bars = reinterpret_cast<uint64_t*>(red + 2 * NW);
   int* slot_row = reinterpret_cast<int*>(bars + stages);
-  __shared__ int s_arrival;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = p.n, m = p.m;
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
     if (blockIdx.x == 0 && tid == 0) {
       *p.ctr_clear = 0;
       *p.arrive_clear = 0;
+      *p.slice_clear = 0;
     }
   }
 
@@ -235,37 +237,22 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
     }
   }
   if (st) atomicOr(&p.ctl->status, st);
-  // The last CTAs: G = (1 - fi) G_prev + R_t^T z; db and the next step's w.
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    s_arrival = atomicAdd(p.arrive, 1);
-  }
-  __syncthreads();
-  const int G = int(gridDim.x);
-  const int K = min(G, BW_BETA_CTAS);
-  const int slice = s_arrival - (G - K);
-  if (slice >= 0) {
-    if (tid == 0) {
-      const uint64_t t0 = global_timer_ns();
-      while (ld_acquire_gpu(p.arrive) < G) {
-        if (global_timer_ns() - t0 > WAIT_LIMIT_NS) {
-          atomicOr(&p.ctl->status, DEV_TIMEOUT);
-          break;
+  // The CTAs that finish last: G = (1 - fi) G_prev + R_t^T z; db and the next
+  // step's w (claimed in column slices once every CTA's partials landed).
+  {
+    const int nsl = 64;
+    const int per = (m + nsl - 1) / nsl;
+    finish_pass_job(p.arrive, p.slice_ctr, nsl, BW_BETA_CTAS, 2000, [&](int sl) {
+      const int j0 = sl * per, j1 = min(m, j0 + per);
+      for (int j = j0 + tid; j < j1; j += THREADS) {
+        const float Gj = p.Gs[j] + __ldcg(p.h_next + j);
+        if (p.t > 1) {
+          p.db[j] += p.fi * Gj / __ldg(p.b + j);
+          p.w[j] = -p.fi * Gj / __ldcg(p.c_prev + j);
+          p.Gs[j] = (1.0f - p.fi) * Gj;
         }
       }
-    }
-    __syncthreads();
-    const int per = (m + K - 1) / K;
-    const int j0 = slice * per, j1 = min(m, j0 + per);
-    for (int j = j0 + tid; j < j1; j += THREADS) {
-      const float Gj = p.Gs[j] + __ldcg(p.h_next + j);
-      if (p.t > 1) {
-        p.db[j] += p.fi * Gj / __ldg(p.b + j);
-        p.w[j] = -p.fi * Gj / __ldcg(p.c_prev + j);
-        p.Gs[j] = (1.0f - p.fi) * Gj;
-      }
-    }
+    });
   }
   if (tid == 0 && broken) {
     for (int q = max(0, issued - stages); q < issued; ++q)
@@ -385,7 +372,7 @@ BwLayout bw_layout(int64_t n, int64_t m) {
   L.Gs = off; off = align256(off + mpad);
   L.G0 = off; off = align256(off + mpad);
   for (int k = 0; k < 3; ++k) { L.h[k] = off; off = align256(off + mpad); }
-  L.ctr = off; off = align256(off + 6 * sizeof(int));
+  L.ctr = off; off = align256(off + 9 * sizeof(int));
   L.total = off;
   return L;
 }
@@ -424,7 +411,10 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
                                  const float* a, const float* b, int64_t n, int64_t m, float reg,
                                  float reg_m, int32_t iters, const void* hist, size_t hist_bytes,
                                  double grad_out, float* dC, int64_t lddc, float* da, float* db,
-                                 void* workspace, size_t ws_bytes, void* stream) {
+                                 void* workspace, size_t ws_bytes, const uot_options* opt,
+                                 void* stream) {
+  const int max_ctas = opt ? opt->max_ctas : 0;
+  if (max_ctas < 0) return UOT_ERR_INVALID_ARG;
   if (!K || !C || !a || !b || !hist || !dC || !da || !db || n < 1 || m < 1 || n > INT32_MAX ||
       m > INT32_MAX / 2 || ldk < m || ldc < m || lddc < m)
     return UOT_ERR_INVALID_ARG;
@@ -521,6 +511,7 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
   const size_t smem = bw_smem(e, best_st);
   int grid = best_occ * sms;
   if (grid > (N + 1) / 2) grid = std::max(1, (N + 1) / 2);
+  if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
 
   BwArgs A{};
   A.K = K;
@@ -555,6 +546,8 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
     A.ctr_clear = ctr + (q + 1) % 3;
     A.arrive = ctr + 3 + q % 3;
     A.arrive_clear = ctr + 3 + (q + 1) % 3;
+    A.slice_ctr = ctr + 6 + q % 3;
+    A.slice_clear = ctr + 6 + (q + 1) % 3;
     void* kargs[] = {&A};
     if (cudaLaunchKernel(e.fn, dim3(grid), dim3(e.threads), kargs, smem, s) != cudaSuccess)
       return UOT_ERR_CUDA;

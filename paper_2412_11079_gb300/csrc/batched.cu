@@ -692,8 +692,23 @@ uot_status uot_sinkhorn_batched(void* workspace, void* stream) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel, BT, smem) != cudaSuccess)
     return UOT_ERR_CUDA;
   if (occ * sms < hp.grid) return UOT_ERR_UNSUPPORTED;
-  batched_kernel<<<hp.grid, BT, smem, s>>>(hp.sched);
-  if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
+  // Team barriers need every CTA resident at once: a cooperative launch
+  // guarantees it (or fails) even when other work shares the GPU.
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.gridDim = dim3(hp.grid);
+  cfg.blockDim = dim3(BT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  BatchSched S = hp.sched;
+  void* kargs[] = {&S};
+  if (cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(batched_kernel), kargs) !=
+      cudaSuccess)
+    return UOT_ERR_CUDA;
   count_launch();
   return UOT_OK;
 }

@@ -51,7 +51,9 @@
 namespace uot {
 
 constexpr int MAX_CLUSTER = 8;
-constexpr int BETA_CTAS = 16;  // CTAs that compute the next column factors
+constexpr int BETA_CTAS = 16;       // late CTAs that may help with the next factors
+constexpr int BETA_SLICES = 64;     // column slices of that job
+constexpr uint64_t HELP_LOOK_NS = 2000;  // how long a late CTA looks for the rest
 
 template <typename T, int THREADS, int KV, bool TMA, bool KF>
 __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs p) {
@@ -212,6 +214,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
     if (blockIdx.x == 0 && tid == 0) {
       *p.ctr_clear = 0;
       *p.arrive_clear = 0;
+      *p.slice_clear = 0;
     }
     if (p.track && blockIdx.x == 0 && tid < 2) p.err_clear[tid] = 0.0;
   }
@@ -389,49 +392,30 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
   if (st) atomicOr(&ctl->status, st);
 
   // beta_t = (b_j / c_j)^fi for the next pass (kernel form: V <- V beta_t),
-  // computed once: the last K CTAs
-  // to finish this pass each take 1/K of the columns, after waiting (bounded)
-  // for every CTA's column partials to land.  Only CTAs already running are
-  // waited for, so this needs no co-residency guarantee.
-  __syncthreads();
-  __shared__ int s_arrival;
-  if (tid == 0) {
-    __threadfence();
-    s_arrival = atomicAdd(p.arrive, 1);
-  }
-  __syncthreads();
-  const int G = int(gridDim.x);
-  const int K = min(G, BETA_CTAS);
-  const int slice = s_arrival - (G - K);
-  if (slice >= 0) {
-    if (tid == 0) {
-      const uint64_t t0 = global_timer_ns();
-      while (ld_acquire_gpu(p.arrive) < G) {
-        if (global_timer_ns() - t0 > WAIT_LIMIT_NS) {
-          atomicOr(&ctl->status, DEV_TIMEOUT);
-          break;
-        }
-      }
-    }
-    __syncthreads();
-    const int per = (m + K - 1) / K;
-    const int j0 = slice * per, j1 = min(m, j0 + per);
+  // computed once per column by the CTAs that finish last, in slices, after
+  // every CTA's column partials have landed.
+  {
+    const int nsl = BETA_SLICES;
+    const int per = (m + nsl - 1) / nsl;
     uint32_t st2 = 0;
-    for (int j = j0 + tid; j < j1; j += THREADS) {
-      if constexpr (KF) {
-        // V_j <- V_j (b_j / c_j)^fi 2^-e_t with c_j = V_j 2^-e_t sum_i U_i K_ij.
-        const float v = __ldcg(p.beta_out + j);
-        const float c = v * __ldcg(p.c_next + j) * inv_gauge;
-        const float v_new = v * rescale_factor(__ldg(p.b_ws + j), c, p.fi, st2) * inv_gauge;
-        p.beta_out[j] = v_new;
-        if (p.save_c) {  // history for the adjoint: c_t and V_t of this column
-          p.save_c[j] = c;
-          p.save_V[j] = v_new;
+    finish_pass_job(p.arrive, p.slice_ctr, nsl, BETA_CTAS, HELP_LOOK_NS, [&](int sl) {
+      const int j0 = sl * per, j1 = min(m, j0 + per);
+      for (int j = j0 + tid; j < j1; j += THREADS) {
+        if constexpr (KF) {
+          // V_j <- V_j (b_j / c_j)^fi 2^-e_t with c_j = V_j 2^-e_t sum_i U_i K_ij.
+          const float v = __ldcg(p.beta_out + j);
+          const float c = v * __ldcg(p.c_next + j) * inv_gauge;
+          const float v_new = v * rescale_factor(__ldg(p.b_ws + j), c, p.fi, st2) * inv_gauge;
+          p.beta_out[j] = v_new;
+          if (p.save_c) {  // history for the adjoint: c_t and V_t of this column
+            p.save_c[j] = c;
+            p.save_V[j] = v_new;
+          }
+        } else {
+          p.beta_out[j] = rescale_factor(__ldg(p.b_ws + j), __ldcg(p.c_next + j), p.fi, st2);
         }
-      } else {
-        p.beta_out[j] = rescale_factor(__ldg(p.b_ws + j), __ldcg(p.c_next + j), p.fi, st2);
       }
-    }
+    });
     if (st2) atomicOr(&ctl->status, st2);
   }
 

@@ -206,7 +206,7 @@ __global__ void reset_kernel(Control* ctl, double* err_ring, float* c1, int mpad
     ctl->err = __longlong_as_double(0x7ff0000000000000ll);
   }
   if (g < 6) err_ring[g] = 0.0;
-  if (g < 6) ctr[g] = 0;
+  if (g < 9) ctr[g] = 0;
   for (int j = g; j < mpad; j += gridDim.x * blockDim.x) {
     c1[j] = 0.0f;
     b_ws[j] = j < m ? b[j] : 0.0f;

@@ -190,6 +190,48 @@ __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
   return v;
 }
 
+// Once-per-pass column job (the next pass's column factors) shared among the
+// CTAs that finish a pass last, with no CTA ever waiting on a CTA that may
+// not be resident: every CTA arrives on `arrive`; the last `helpers` to
+// arrive look (for at most `look_ns`) for the count to reach the grid size,
+// and those that see it claim slices from `slice_ctr` until all `nslices`
+// are taken.  The very last arrival always sees the full count, so every
+// slice is done exactly once, after all CTAs' earlier writes (made visible
+// by the fence before each arrival).  Calls job(slice) for claimed slices.
+template <typename Job>
+__device__ __forceinline__ void finish_pass_job(int* arrive, int* slice_ctr, int nslices,
+                                                int helpers, uint64_t look_ns, Job&& job) {
+  __shared__ int s_arrival, s_all, s_slice;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_arrival = atomicAdd(arrive, 1);
+  }
+  __syncthreads();
+  const int G = int(gridDim.x);
+  if (s_arrival < G - helpers) return;  // uniform for the CTA
+  if (threadIdx.x == 0) {
+    bool all = s_arrival == G - 1;
+    if (!all) {
+      const uint64_t t0 = global_timer_ns();
+      while (!(all = ld_acquire_gpu(arrive) >= G))
+        if (global_timer_ns() - t0 > look_ns) break;
+    }
+    __threadfence();
+    s_all = all ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_all) return;
+  while (true) {
+    if (threadIdx.x == 0) s_slice = atomicAdd(slice_ctr, 1);
+    __syncthreads();
+    const int sl = s_slice;
+    __syncthreads();
+    if (sl >= nslices) break;
+    job(sl);
+  }
+}
+
 // ----------------------------------------------------------------- cluster
 __device__ __forceinline__ uint32_t cluster_ctarank() {
   uint32_t r;

@@ -36,7 +36,7 @@ struct WsLayout {
   size_t f;       // float[npad]: row factors (multi-pass algorithm)
   size_t g;       // float[mpad]: column factors (multi-pass algorithm)
   size_t bws;     // float[mpad]: copy of b, zero-padded (aligned vector loads)
-  size_t ctr;     // int32[6]: per-pass row counters and arrival counters, rings of 3
+  size_t ctr;     // int32[9]: per-pass row, arrival and slice counters, rings of 3
   size_t beta;    // float[mpad]: column factors of the last completed pass
   size_t log2k;   // double: log2 of the fixed-point row factor (kernel-form gauge)
   size_t total;
@@ -57,7 +57,7 @@ inline WsLayout ws_layout(int64_t n, int64_t m) {
   L.f = off; off = align256(off + size_t(L.npad) * 4);
   L.g = off; off = align256(off + size_t(L.mpad) * 4);
   L.bws = off; off = align256(off + size_t(L.mpad) * 4);
-  L.ctr = off; off = align256(off + 6 * sizeof(int32_t));
+  L.ctr = off; off = align256(off + 9 * sizeof(int32_t));
   L.beta = off; off = align256(off + size_t(L.mpad) * 4);
   L.log2k = off; off = align256(off + sizeof(double));
   L.total = off;
@@ -93,6 +93,8 @@ struct FusedArgs {
   int dynamic;         // 1: dynamic row schedule (single-CTA rows, bulk copies)
   int* arrive;         // CTAs that finished this pass
   int* arrive_clear;   // arrival counter to clear for iteration t+1
+  int* slice_ctr;      // column slices of the end-of-pass job taken so far
+  int* slice_clear;    // slice counter to clear for iteration t+1
   float* U;            // kernel form: row scalings (read and updated per row)
   const double* log2k; // kernel form: log2 k for the power-of-two gauge
   const float* beta;   // beta_{t-1}, zero-padded to mpad (read unless first)

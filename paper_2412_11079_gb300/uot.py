@@ -33,7 +33,8 @@ UOT_DEV_ZERO_SUM, UOT_DEV_NONFINITE, UOT_DEV_TIMEOUT = 1, 2, 4
 class UotOptions(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("algo", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("cluster", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+                ("cluster", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2),
                 ("pass_events", ctypes.c_void_p * 2)]
 
 
@@ -91,7 +92,8 @@ SIGNATURES = {
                                                ctypes.POINTER(UotResult)]),
     "uot_backward_workspace_size": (_SZ, [_I64, _I64]),
     "uot_sinkhorn_backward": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _P, _I64, _I64, _F, _F,
-                                             _I32, _P, _SZ, _D, _P, _I64, _P, _P, _P, _SZ, _P]),
+                                             _I32, _P, _SZ, _D, _P, _I64, _P, _P, _P, _SZ,
+                                             ctypes.POINTER(UotOptions), _P]),
     "uot_sinkhorn_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _D,
                                             ctypes.POINTER(UotOptions), _P,
                                             ctypes.POINTER(UotResult)]),
@@ -171,10 +173,11 @@ def _stream(stream):
 
 
 def options(dtype: int = UOT_F32, algo: int = UOT_ALGO_FUSED, check_every: int = 1,
-            tile: int = 0, cluster: int = 0) -> UotOptions:
+            tile: int = 0, cluster: int = 0, max_ctas: int = 0) -> UotOptions:
     o = UotOptions()
     load().uot_default_options(ctypes.byref(o))
     o.dtype, o.algo, o.check_every, o.tile, o.cluster = dtype, algo, check_every, tile, cluster
+    o.max_ctas = max_ctas
     return o
 
 
@@ -435,7 +438,7 @@ def uot_batched_results(ws, nprob: int, stream=None, check_status: bool = True):
 
 
 def uot_sinkhorn_kform_save(K, a, b, reg: float, reg_m: float, iters: int, U=None, V=None,
-                            hist=None, ws=None, stream=None):
+                            hist=None, ws=None, stream=None, opt: UotOptions | None = None):
     """Kernel-form solve of exactly `iters` iterations that keeps the history
     its adjoint needs; returns (U, V, hist)."""
     torch = _torch()
@@ -454,14 +457,15 @@ def uot_sinkhorn_kform_save(K, a, b, reg: float, reg_m: float, iters: int, U=Non
                                           float(reg), float(reg_m), int(iters), 0.0,
                                           _vector(U, "U", n), _vector(V, "V", m),
                                           hist.data_ptr(), hist.numel(), ws.data_ptr(),
-                                          ws.numel(), None, _stream(stream), None),
+                                          ws.numel(), ctypes.byref(opt) if opt else None,
+                                          _stream(stream), None),
            "uot_sinkhorn_kform_save")
     return U, V, hist
 
 
 def uot_sinkhorn_backward(K, C, a, b, reg: float, reg_m: float, iters: int, hist,
                           grad_out: float = 1.0, dC=None, da=None, db=None, ws=None,
-                          stream=None):
+                          stream=None, opt: UotOptions | None = None):
     torch = _torch()
     n, m = K.shape
     dC = torch.empty((n, (m + 3) // 4 * 4), device=K.device)[:, :m] if dC is None else dC
@@ -476,6 +480,7 @@ def uot_sinkhorn_backward(K, C, a, b, reg: float, reg_m: float, iters: int, hist
                                         n, m, float(reg), float(reg_m), int(iters),
                                         hist.data_ptr(), hist.numel(), float(grad_out), gp, ldd,
                                         _vector(da, "da", n), _vector(db, "db", m),
-                                        ws.data_ptr(), ws.numel(), _stream(stream)),
+                                        ws.data_ptr(), ws.numel(),
+                                        ctypes.byref(opt) if opt else None, _stream(stream)),
            "uot_sinkhorn_backward")
     return dC, da, db

@@ -39,7 +39,7 @@ def test_status_strings_and_defaults(lib):
     assert "workspace" in uot.uot_status_string(uot.UOT_ERR_WORKSPACE)
     o = uot.UotOptions()
     lib.uot_default_options(ctypes.byref(o))
-    assert (o.dtype, o.algo, o.check_every, o.tile, o.cluster) == (0, 0, 1, 0, 0)
+    assert (o.dtype, o.algo, o.check_every, o.tile, o.cluster, o.max_ctas) == (0, 0, 1, 0, 0, 0)
 
 
 def test_workspace_size(lib):
@@ -88,7 +88,7 @@ def test_argument_validation_needs_no_gpu(lib):
     assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, ctypes.c_void_p(4096 + 8), 1 << 20,
              ctypes.byref(o), None, None) == uot.UOT_ERR_WORKSPACE
     # bad dtype, nonzero reserved, cluster out of range
-    for field, val in [("dtype", 7), ("cluster", 9), ("algo", 3)]:
+    for field, val in [("dtype", 7), ("cluster", 9), ("algo", 3), ("max_ctas", -1)]:
         bad = uot.options()
         setattr(bad, field, val)
         assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 1 << 20, ctypes.byref(bad), None,
