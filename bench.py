@@ -281,6 +281,11 @@ def run_batched(args):
     res = B.results()
     assert all(r.dev_status == 0 for r in res)
     elems = B.element_iterations
+    place = B.placement()
+    engines = {"on_chip_problems": sum(1 for c in place if c),
+               "on_chip_elements": sum(int(pl.numel()) for pl, c in zip(B.plans, place) if c),
+               "streaming_problems": sum(1 for c in place if not c),
+               "cluster_sizes": {str(k): place.count(k) for k in sorted(set(place)) if k}}
     # Loops of single-problem launches on the same problems: the in-place
     # fused path, and the kernel form (what the batched engine runs).
     opt = uot.options()
@@ -317,7 +322,9 @@ def run_batched(args):
         "batched": {"ms": ms, "elems_per_s": elems / (ms * 1e-3),
                     "alg_gbs": alg_bytes / (ms * 1e-3) / 1e9,
                     "tuning": {"stages": best.stages, "max_team": best.max_team,
-                               "target_elems": best.target_elems}},
+                               "target_elems": best.target_elems,
+                               "resident_max_cluster": best.resident_max_cluster},
+                    "engines": engines},
         "looped_single_launches": {k: {"ms": v, "elems_per_s": elems / (v * 1e-3)}
                                    for k, v in loop_ms.items()},
         "batched_over_loop": {k: v / ms for k, v in loop_ms.items()},

@@ -295,12 +295,19 @@ uot_status uot_sinkhorn_noalloc(void* plan, int64_t ldp, const float* a, const f
                                 uot_result* out);
 
 /*
- * Batched iteration: many independent problems of uneven size in one
- * persistent launch (Section 2.1 rule, one sweep per iteration as in
- * Algorithm 1; FP32 plans in place).  Problems are grouped into size classes
- * served by teams of CTAs (a power of two, more CTAs for larger problems);
- * inside a team, rows are shared dynamically and the team meets at a bounded
- * software barrier once per iteration.
+ * Batched iteration: many independent problems of uneven size (Section 2.1
+ * rule, one sweep per iteration as in Algorithm 1; FP32 plans, overwritten
+ * by the result).  Two engines share a batch:
+ *   on chip    a problem whose initial plan fits in the shared memory of one
+ *              CTA or of a cluster of up to 16 CTAs keeps it there for all
+ *              its iterations (one launch per cluster size, each cluster
+ *              taking problems from a queue; cluster barriers and
+ *              distributed shared memory for the column sums);
+ *   streaming  the others are grouped into size classes served by teams of
+ *              CTAs (a power of two, more CTAs for larger problems) in one
+ *              persistent cooperative launch; inside a team, rows are shared
+ *              dynamically and the team meets at a bounded software barrier
+ *              once per iteration.
  */
 typedef struct uot_problem {
   void* plan;        /* device, n x m FP32, row-major; 16-byte aligned, ldp % 4 == 0 */
@@ -314,16 +321,22 @@ typedef struct uot_problem {
 } uot_problem;
 
 /* Schedule knobs (uot_batch_default_tuning fills the defaults):
- *   stages        ring depth per CTA (2..8 slots of 16 KB);
- *   max_team      largest team size (a power of two);
+ *   stages        ring depth per streaming CTA (2..8 slots of 16 KB);
+ *   max_team      largest streaming team size (a power of two);
  *   target_elems  element-iterations per CTA used to size the teams: a
  *                 problem of N*M*(iters+1) element-iterations gets the
- *                 smallest power-of-two team with team * target >= work. */
+ *                 smallest power-of-two team with team * target >= work;
+ *   resident_max_cluster
+ *                 largest cluster for on-chip solves (0, 1, 2, 4, 8 or 16;
+ *                 0 sends every problem to the streaming engine).  A problem
+ *                 goes on chip with the smallest cluster that holds it;
+ *   reserved      must be 0. */
 typedef struct uot_batch_tuning {
   int32_t stages;
   int32_t max_team;
   double target_elems;
-  int32_t reserved[4];
+  int32_t resident_max_cluster;
+  int32_t reserved[3];
 } uot_batch_tuning;
 
 void uot_batch_default_tuning(uot_batch_tuning* t);
@@ -339,9 +352,16 @@ uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uo
                                const uot_batch_tuning* tuning, void* workspace,
                                size_t ws_bytes, void* stream);
 
-/* Runs every prepared problem: one reset launch and one persistent launch,
- * fully asynchronous (capturable in a CUDA graph once prepared). */
+/* Runs every prepared problem: one reset launch, one launch per on-chip
+ * cluster size in use and one persistent streaming launch (when any problem
+ * streams), fully asynchronous (capturable in a CUDA graph once prepared). */
 uot_status uot_sinkhorn_batched(void* workspace, void* stream);
+
+/* Where prepare put each problem: cluster[i] = the on-chip cluster size
+ * (1..16) or 0 for the streaming engine, for i < min(nprob, prepared count).
+ * Host only; returns the prepared count, or -1 for a workspace that was never
+ * prepared.  `cluster` may be NULL. */
+int32_t uot_batched_placement(const void* workspace, int32_t nprob, int32_t* cluster);
 
 /* Synchronises `stream` and copies each problem's result to out[0..nprob). */
 uot_status uot_batched_results(const void* workspace, int32_t nprob, uot_result* out,

@@ -63,6 +63,10 @@ class Batch:
     def run(self, stream=None):
         uot.uot_sinkhorn_batched(self.ws, stream)
 
+    def placement(self):
+        """On-chip cluster size per problem (0: streaming engine)."""
+        return uot.uot_batched_placement(self.ws, len(self.descs))
+
     def results(self, stream=None, check_status=True):
         return uot.uot_batched_results(self.ws, len(self.descs), stream, check_status)
 

@@ -80,9 +80,7 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = p.n, m = p.m;
-  const double L2k = *p.log2k;
-  const float qscale =
-      ldexpf(1.0f, -int(rint(-double(p.t) * L2k) - rint(-double(p.t - 1) * L2k)));
+  const float qscale = ldexpf(1.0f, -gauge_exponent(p.t, float(*p.log2k)));
   const uint32_t copy_bytes = uint32_t((size_t(m) * 4) & ~size_t(15));
   uint32_t st = 0;
 
@@ -142,6 +140,17 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
 
   bool broken = false;
   int done_rows = 0;
+  // Per-row values of the next step, loaded one step ahead (its row was
+  // armed before this step's barrier) so their latency overlaps this step.
+  float pf[5];
+  bool have_pf = false;
+  auto fetch_row = [&](int row, float (&v5)[5]) {
+    v5[0] = __ldcg(p.q + row);
+    v5[1] = __ldcg(p.pr + row);
+    v5[2] = __ldcg(p.r + row);
+    v5[3] = __ldg(p.a + row);
+    v5[4] = __ldcg(p.F + row);
+  };
   for (int q = 0;; ++q) {
     const int slot = q % stages;
     if (!broken && !mbar_wait_bounded(&bars[slot], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS)) {
@@ -150,11 +159,18 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
     }
     const int row = *reinterpret_cast<volatile int*>(&slot_row[slot]);
     if (row < 0 || row >= n) break;
-    const float qi = __ldcg(p.q + row) * qscale;
-    const float pi = __ldcg(p.pr + row);
-    const float ri = __ldcg(p.r + row);
-    const float ai = __ldg(p.a + row);
-    const float Fi = __ldcg(p.F + row);
+    float cur[5];
+    if (have_pf) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) cur[i] = pf[i];
+    } else {
+      fetch_row(row, cur);
+    }
+    const float qi = cur[0] * qscale;
+    const float pi = cur[1];
+    const float ri = cur[2];
+    const float ai = cur[3];
+    const float Fi = cur[4];
     const unsigned char* sK = ring + size_t(slot) * 2 * ROW_BYTES;
     const unsigned char* sD = sK + ROW_BYTES;
     const float* gK = p.K + int64_t(row) * p.ldk;
@@ -185,6 +201,13 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
       broken = true;
       st |= DEV_TIMEOUT;
       break;
+    }
+    {
+      // Step q + 1 was armed at step q + 1 - stages (or before the loop),
+      // ahead of this barrier; its slot is re-armed only after the next one.
+      const int nrow = *reinterpret_cast<volatile int*>(&slot_row[(q + 1) % stages]);
+      have_pf = nrow >= 0 && nrow < n;
+      if (have_pf) fetch_row(nrow, pf);
     }
     if (tid == 0 && !broken) {
       const int r2 = next_row;

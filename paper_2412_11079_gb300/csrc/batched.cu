@@ -36,6 +36,7 @@
 #include <mutex>
 #include <vector>
 
+#include "batched_internal.h"
 #include "uot_device.cuh"
 #include "uot_internal.h"
 
@@ -47,24 +48,10 @@ constexpr int BT = 256;           // threads per CTA
 constexpr int BKV = 4;            // 16-byte vectors per thread per row
 constexpr int BW = BT * BKV * 4;  // widest row (FP32 columns)
 constexpr int MAX_CLASSES = 8;
+constexpr int MAX_RES_CLASSES = 5;  // on-chip cluster sizes 1, 2, 4, 8, 16
+constexpr int CURSORS = MAX_CLASSES + MAX_RES_CLASSES;
 constexpr int MAX_STAGES = 8;
 constexpr int SLOT_BYTES = BT * BKV * 16;
-
-struct BatchProblem {
-  float* plan;
-  int64_t ldp;
-  int n, m;
-  const float* a;
-  const float* b;
-  float fi;
-  int iters;
-  int mpad;
-  float* c;       // 3 x mpad column sums of U K (ring)
-  int* ctr;       // 3 row counters (ring)
-  float* U;       // n row scalings
-  double* log2k;  // log2 of the fixed-point row factor (gauge)
-  Control* ctl;
-};
 
 struct BatchSched {
   int nprob;
@@ -186,6 +173,10 @@ __device__ void sweep(const BatchProblem& P, bool finish, const float (&V)[BKV][
       ++issued;
     }
   }
+  // U_i and a_i of the next step's rows, loaded one step ahead so that their
+  // latency overlaps this step.
+  float u_pf = 0.0f, a_pf = 0.0f;
+  bool have_pf = false;
   int q = qbase;
   for (;; ++q) {
     const int slot = q % stages;
@@ -204,7 +195,14 @@ __device__ void sweep(const BatchProblem& P, bool finish, const float (&V)[BKV][
     float* grow = plan + int64_t(live ? row : 0) * ldp;
     float x[BKV][4];
     float s = 0.0f;
-    const float u_old = live ? __ldcg(P.U + row) : 0.0f;
+    float u_old = 0.0f, a_row = 0.0f;
+    if (have_pf) {
+      u_old = u_pf;
+      a_row = a_pf;
+    } else if (live) {
+      u_old = __ldcg(P.U + row);
+      if (!finish) a_row = __ldg(P.a + row);
+    }
 #pragma unroll
     for (int k = 0; k < BKV; ++k) {
       const int ch = l + k * gt;
@@ -229,6 +227,14 @@ __device__ void sweep(const BatchProblem& P, bool finish, const float (&V)[BKV][
       broken = true;
       st |= DEV_TIMEOUT;
       break;
+    }
+    {
+      // Step q + 1 was armed at step q + 1 - stages (or before the loop),
+      // ahead of this barrier; its slot is re-armed only after the next one.
+      const int nrow = *reinterpret_cast<volatile int*>(&slot_rows[((q + 1) % stages) * BT + g]);
+      have_pf = true;
+      u_pf = nrow >= 0 ? __ldcg(P.U + nrow) : 0.0f;
+      a_pf = (nrow >= 0 && !finish) ? __ldg(P.a + nrow) : 0.0f;
     }
     if (tid == 0 && more) {
       more = arm(issued);
@@ -257,7 +263,7 @@ __device__ void sweep(const BatchProblem& P, bool finish, const float (&V)[BKV][
       }
       continue;
     }
-    const float u_new = u_old * rescale_factor(__ldg(P.a + row), u_old * s, P.fi, st) * gauge;
+    const float u_new = u_old * rescale_factor(a_row, u_old * s, P.fi, st) * gauge;
     if (l == 0) P.U[row] = u_new;
 #pragma unroll
     for (int k = 0; k < BKV; ++k)
@@ -358,7 +364,7 @@ __global__ void __launch_bounds__(BT, 2) batched_kernel(const BatchSched S) {
         for (int e = 0; e < 4; ++e) V[k][e] = ((l + k * gt) * 4 + e < P.m) ? 1.0f : 0.0f;
       // The scalings drift as U ~ k^t, V ~ k^-t (row factors tend to k at the
       // fixed point); an exact power of two moves between them every pass.
-      const double L = *P.log2k;
+      const float Lf = float(*P.log2k);
       float gauge = 1.0f, inv_gauge = 1.0f;
       for (int t = 1; t <= P.iters + 1 && !broken; ++t) {
         const bool finish = t == P.iters + 1;
@@ -376,7 +382,7 @@ __global__ void __launch_bounds__(BT, 2) batched_kernel(const BatchSched S) {
             }
         }
         if (!finish) {
-          const int ex = int(rint(-double(t) * L) - rint(-double(t - 1) * L));
+          const int ex = gauge_exponent(t, Lf);
           gauge = ldexpf(1.0f, ex);
           inv_gauge = ldexpf(1.0f, -ex);
         }
@@ -440,7 +446,7 @@ __global__ void batched_reset_kernel(const BatchProblem* probs, int nprob, int* 
     }
   }
   if (p == 0) {
-    for (int i = threadIdx.x; i < MAX_CLASSES; i += blockDim.x) cursor[i] = 0;
+    for (int i = threadIdx.x; i < CURSORS; i += blockDim.x) cursor[i] = 0;
     for (int i = threadIdx.x; i < nteams; i += blockDim.x) {
       mailbox[i] = -1;
       bar[2 * i] = 0;
@@ -469,11 +475,18 @@ static size_t per_problem_bytes(int64_t n, int64_t m) {
 // What a launch needs on the host, recorded by uot_batched_prepare for its
 // workspace (a launch may be captured in a CUDA graph, so it cannot read the
 // device copy back).
+struct ResClass {
+  int cs, begin, count, grid;
+  size_t smem;
+};
 struct HostPlan {
   const void* ws;
   int grid, stages, nprob, teams;
-  size_t probs_off, cursor_off, mailbox_off, bar_off, ctl_off;
+  size_t probs_off, order_off, cursor_off, mailbox_off, bar_off, ctl_off;
   BatchSched sched;
+  int nres;
+  ResClass res[MAX_RES_CLASSES];
+  std::vector<int8_t> placement;  // per problem: on-chip cluster size, 0 = streaming
 };
 static std::mutex g_plan_mu;
 static std::vector<HostPlan> g_plans;
@@ -501,7 +514,7 @@ size_t uot_batched_workspace_size(const uot_problem* probs, int32_t nprob, const
   if (!probs || nprob <= 0) return 0;
   size_t total = a256(sizeof(BatchHeader)) + a256(sizeof(BatchSched)) +
                  a256(size_t(nprob) * sizeof(BatchProblem)) + a256(size_t(nprob) * 4) +
-                 a256(MAX_CLASSES * 4) + a256(size_t(max_teams_bound(nprob)) * 4) +
+                 a256(CURSORS * 4) + a256(size_t(max_teams_bound(nprob)) * 4) +
                  a256(size_t(max_teams_bound(nprob)) * 8) + a256(size_t(nprob) * sizeof(Control));
   for (int i = 0; i < nprob; ++i) {
     if (probs[i].n < 1 || probs[i].m < 1) return 0;
@@ -534,7 +547,10 @@ uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uo
   uot_batch_default_tuning(&tu);
   if (tuning) tu = *tuning;
   if (tu.stages < 2 || tu.stages > MAX_STAGES || tu.target_elems <= 0 || tu.max_team < 1 ||
-      tu.max_team > 1024 || (tu.max_team & (tu.max_team - 1)))
+      tu.max_team > 1024 || (tu.max_team & (tu.max_team - 1)) || tu.resident_max_cluster < 0 ||
+      tu.resident_max_cluster > RESIDENT_MAX_CLUSTER ||
+      (tu.resident_max_cluster & (tu.resident_max_cluster - 1)) || tu.reserved[0] ||
+      tu.reserved[1] || tu.reserved[2])
     return UOT_ERR_INVALID_ARG;
 
   int dev = 0, sms = 0;
@@ -552,12 +568,34 @@ uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uo
     return UOT_ERR_CUDA;
   const int grid = occ * sms;
 
-  // Classes: team size = clamp(next power of two of N*M*iters / target), so
-  // every CTA of a team gets about `target_elems` element-iterations.
-  std::vector<int> gsize(nprob);
+  // On chip: the smallest cluster (up to resident_max_cluster) whose shared
+  // memory holds the problem; rescls[i] = index of that cluster size, or -1.
   std::vector<double> work(nprob);
-  for (int i = 0; i < nprob; ++i) {
+  for (int i = 0; i < nprob; ++i)
     work[i] = double(probs[i].n) * double(probs[i].m) * double(probs[i].iters + 1);
+  std::vector<int> rescls(nprob, -1);
+  int res_clusters[MAX_RES_CLASSES] = {0, 0, 0, 0, 0};
+  size_t res_cap = 0;
+  if (tu.resident_max_cluster > 0) {
+    if (resident_smem_cap(&res_cap) != cudaSuccess) return UOT_ERR_CUDA;
+    for (int c = 0; c < MAX_RES_CLASSES && (1 << c) <= tu.resident_max_cluster; ++c)
+      if (resident_max_clusters(1 << c, res_cap, &res_clusters[c]) != cudaSuccess)
+        return UOT_ERR_CUDA;
+    for (int i = 0; i < nprob; ++i)
+      for (int c = 0; c < MAX_RES_CLASSES && (1 << c) <= tu.resident_max_cluster; ++c)
+        if (res_clusters[c] > 0 &&
+            resident_smem_need(probs[i].n, probs[i].m, 1 << c) <= res_cap) {
+          rescls[i] = c;
+          break;
+        }
+  }
+
+  // Streaming classes: team size = clamp(next power of two of N*M*iters /
+  // target), so every CTA of a team gets about `target_elems`
+  // element-iterations.
+  std::vector<int> gsize(nprob, 0);
+  for (int i = 0; i < nprob; ++i) {
+    if (rescls[i] >= 0) continue;
     int g = 1;
     while (g < tu.max_team && g * 2 <= grid && double(g) * tu.target_elems < work[i]) g <<= 1;
     gsize[i] = g;
@@ -571,7 +609,7 @@ uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uo
       }
   if (int(classes.size()) > MAX_CLASSES) {  // merge the smallest classes into size 1
     for (int i = 0; i < nprob; ++i)
-      if (gsize[i] < classes[MAX_CLASSES - 1]) gsize[i] = classes[MAX_CLASSES - 1];
+      if (gsize[i] > 0 && gsize[i] < classes[MAX_CLASSES - 1]) gsize[i] = classes[MAX_CLASSES - 1];
     classes.resize(MAX_CLASSES);
   }
 
@@ -587,7 +625,7 @@ uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uo
   const size_t order_off = off;
   off += a256(size_t(nprob) * 4);
   const size_t cursor_off = off;
-  off += a256(MAX_CLASSES * 4);
+  off += a256(CURSORS * 4);
   const size_t mailbox_off = off;
   off += a256(size_t(max_teams_bound(nprob)) * 4);
   const size_t bar_off = off;
@@ -640,6 +678,30 @@ uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uo
     teams += grid / g;
   }
   if (teams > max_teams_bound(nprob)) return UOT_ERR_UNSUPPORTED;
+  // On-chip classes, after the streaming ones in `order`.
+  ResClass res[MAX_RES_CLASSES];
+  int nres = 0;
+  for (int c = 0; c < MAX_RES_CLASSES; ++c) {
+    std::vector<int> idx;
+    size_t smem = 0;
+    for (int i = 0; i < nprob; ++i)
+      if (rescls[i] == c) {
+        idx.push_back(i);
+        smem = std::max(smem, resident_smem_need(probs[i].n, probs[i].m, 1 << c));
+      }
+    if (idx.empty()) continue;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return work[x] > work[y]; });
+    ResClass& rc = res[nres++];
+    rc.cs = 1 << c;
+    rc.begin = pos;
+    rc.count = int(idx.size());
+    for (int i : idx) order[pos++] = i;
+    int nc = 0;
+    if (resident_max_clusters(rc.cs, smem, &nc) != cudaSuccess) return UOT_ERR_CUDA;
+    if (nc <= 0) return UOT_ERR_UNSUPPORTED;
+    rc.grid = std::min(nc, rc.count) * rc.cs;
+    rc.smem = smem;
+  }
   S.probs = reinterpret_cast<const BatchProblem*>(ws + probs_off);
   S.order = reinterpret_cast<const int*>(ws + order_off);
   S.cursor = reinterpret_cast<int*>(ws + cursor_off);
@@ -660,8 +722,11 @@ uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uo
     return UOT_ERR_CUDA;
   // The host copy must outlive the asynchronous transfer.
   if (cudaStreamSynchronize(s) != cudaSuccess) return UOT_ERR_CUDA;
-  HostPlan hp{workspace, grid, tu.stages, nprob, teams, probs_off, cursor_off,
-              mailbox_off,   bar_off, ctl_off,  S};
+  HostPlan hp{workspace, grid,        tu.stages,   nprob,   teams, probs_off, order_off,
+              cursor_off, mailbox_off, bar_off,     ctl_off, S,     nres,      {}};
+  for (int c = 0; c < nres; ++c) hp.res[c] = res[c];
+  hp.placement.resize(size_t(nprob));
+  for (int i = 0; i < nprob; ++i) hp.placement[i] = int8_t(rescls[i] >= 0 ? 1 << rescls[i] : 0);
   std::lock_guard<std::mutex> lock(g_plan_mu);
   for (HostPlan& h : g_plans)
     if (h.ws == workspace) {
@@ -683,6 +748,15 @@ uot_status uot_sinkhorn_batched(void* workspace, void* stream) {
       reinterpret_cast<int*>(ws + hp.bar_off), hp.teams);
   if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
   count_launch();
+  for (int c = 0; c < hp.nres; ++c) {
+    const ResClass& rc = hp.res[c];
+    if (resident_launch(reinterpret_cast<const BatchProblem*>(ws + hp.probs_off),
+                        reinterpret_cast<const int*>(ws + hp.order_off) + rc.begin, rc.count,
+                        reinterpret_cast<int*>(ws + hp.cursor_off) + MAX_CLASSES + c, rc.cs,
+                        rc.grid, rc.smem, s) != cudaSuccess)
+      return UOT_ERR_CUDA;
+  }
+  if (hp.sched.nclass == 0) return UOT_OK;
   // All CTAs must be resident at once (team barriers): the grid is the
   // occupancy recorded at preparation, re-checked here.
   int dev = 0, sms = 0, occ = 0;
@@ -737,12 +811,21 @@ uot_status uot_batched_results(const void* workspace, int32_t nprob, uot_result*
   return UOT_OK;
 }
 
+int32_t uot_batched_placement(const void* workspace, int32_t nprob, int32_t* cluster) {
+  HostPlan hp;
+  if (!workspace || !find_plan(workspace, &hp)) return -1;
+  if (cluster)
+    for (int i = 0; i < std::min(nprob, hp.nprob); ++i) cluster[i] = hp.placement[i];
+  return hp.nprob;
+}
+
 void uot_batch_default_tuning(uot_batch_tuning* t) {
   if (!t) return;
   std::memset(t, 0, sizeof(*t));
   t->stages = 4;
   t->max_team = 32;
   t->target_elems = 4.0e7;
+  t->resident_max_cluster = RESIDENT_MAX_CLUSTER;
 }
 
 }  // extern "C"

@@ -85,12 +85,12 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
   if (p.track) {
     if (*reinterpret_cast<volatile int32_t*>(&ctl->done)) return;
     if (p.check_prev) {
+      // err = num / den <= tol, decided without the (slow) FP64 division.
       const double num = p.err_prev[0], den = p.err_prev[1];
-      const double e = den > 0.0 ? num / den : __longlong_as_double(0x7ff0000000000000ll);
-      if (e <= p.tol) {
+      if (den > 0.0 && num <= p.tol * den) {
         if (blockIdx.x == 0 && tid == 0) {
           ctl->stop_iter = p.t - 1;
-          ctl->err = e;
+          ctl->err = num / den;
           __threadfence();
           ctl->done = 1;
         }
@@ -106,11 +106,10 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
   // every row factor tends to k and every column factor to 1/k), which leaves
   // FP32's range within a few hundred iterations.  The plan U K V does not
   // change if U is multiplied by 2^e and V by 2^-e, so each pass applies the
-  // exact power-of-two gauge e_t = rint(-t log2 k) - rint(-(t-1) log2 k).
+  // exact power-of-two gauge 2^e_t (gauge_exponent).
   float gauge = 1.0f, inv_gauge = 1.0f;
   if constexpr (KF) {
-    const double L = *p.log2k;
-    const int e = int(rint(-double(p.t) * L) - rint(-double(p.t - 1) * L));
+    const int e = gauge_exponent(p.t, float(*p.log2k));
     gauge = ldexpf(1.0f, e);
     inv_gauge = ldexpf(1.0f, -e);
   }
@@ -227,7 +226,9 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
 
   bool broken = false;
   int done_rows = 0;
-  double err_num = 0.0, err_den = 0.0;
+  // Stopping-rule sums of this CTA's rows (FP32 with compensation; folded
+  // into the FP64 totals once per CTA).
+  float err_num = 0.0f, err_den = 0.0f, err_num_c = 0.0f, err_den_c = 0.0f;
 
   for (int q = 0;; ++q) {
     int row;
@@ -361,9 +362,14 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
       }
     }
     if (p.track && cr == 0 && tid == 0) {
-      const double d = tot;
-      if (p.t >= 2) err_num += fabs(d - double(p.r_prev[row]));
-      err_den += d;
+      auto kahan = [](float& sum, float& comp, float v) {
+        const float y = v - comp;
+        const float t2 = sum + y;
+        comp = (t2 - sum) - y;
+        sum = t2;
+      };
+      if (p.t >= 2) kahan(err_num, err_num_c, fabsf(tot - p.r_prev[row]));
+      kahan(err_den, err_den_c, tot);
       p.r_prev[row] = tot;
     }
     ++done_rows;
@@ -386,8 +392,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
     }
   }
   if (p.track && cr == 0 && tid == 0 && done_rows > 0) {
-    atomicAdd(&p.err_next[0], err_num);
-    atomicAdd(&p.err_next[1], err_den);
+    atomicAdd(&p.err_next[0], double(err_num) - double(err_num_c));
+    atomicAdd(&p.err_next[1], double(err_den) - double(err_den_c));
   }
   if (st) atomicOr(&ctl->status, st);
 

@@ -91,6 +91,15 @@ __device__ __forceinline__ float rescale_factor(float target, float total, float
   return f;
 }
 
+// Exponent of the kernel form's power-of-two gauge at iteration t,
+// e_t = rint(-t log2 k) - rint(-(t-1) log2 k), from log2 k rounded to FP32:
+// integer and FP32 arithmetic only (FP64 is slow on this part).  The forward
+// solve and the adjoint must use the same sequence; any integer sequence
+// leaves the plan diag(U) K diag(V) unchanged.
+__device__ __forceinline__ int gauge_exponent(int t, float log2k) {
+  return __float2int_rn(-float(t) * log2k) - __float2int_rn(-float(t - 1) * log2k);
+}
+
 // ------------------------------------------------------------------- PTX
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -265,6 +274,19 @@ __device__ __forceinline__ uint32_t map_shared_rank(const void* p, uint32_t rank
 }
 __device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, const float4& v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// Barrier `id` (1..15) over `nthreads` threads (a multiple of 32) of the CTA.
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -52,7 +52,8 @@ class UotProblem(ctypes.Structure):
 
 class UotBatchTuning(ctypes.Structure):
     _fields_ = [("stages", ctypes.c_int32), ("max_team", ctypes.c_int32),
-                ("target_elems", ctypes.c_double), ("reserved", ctypes.c_int32 * 4)]
+                ("target_elems", ctypes.c_double), ("resident_max_cluster", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class UotError(RuntimeError):
@@ -105,6 +106,7 @@ SIGNATURES = {
                                            ctypes.POINTER(UotBatchTuning), _P, _SZ, _P]),
     "uot_sinkhorn_batched": (ctypes.c_int, [_P, _P]),
     "uot_batched_results": (ctypes.c_int, [_P, _I32, ctypes.POINTER(UotResult), _P]),
+    "uot_batched_placement": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
     "uot_fused_config": (_I32, [_I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                 ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
 }
@@ -400,7 +402,8 @@ def solve(C, a, b, reg: float, reg_m: float = math.inf, iters: int = 100, tol: f
 
 
 def batch_tuning(stages: int | None = None, max_team: int | None = None,
-                 target_elems: float | None = None) -> UotBatchTuning:
+                 target_elems: float | None = None,
+                 resident_max_cluster: int | None = None) -> UotBatchTuning:
     t = UotBatchTuning()
     load().uot_batch_default_tuning(ctypes.byref(t))
     if stages is not None:
@@ -409,6 +412,8 @@ def batch_tuning(stages: int | None = None, max_team: int | None = None,
         t.max_team = max_team
     if target_elems is not None:
         t.target_elems = target_elems
+    if resident_max_cluster is not None:
+        t.resident_max_cluster = resident_max_cluster
     return t
 
 
@@ -426,6 +431,15 @@ def uot_batched_prepare(probs, ws, tuning: UotBatchTuning | None = None, stream=
 
 def uot_sinkhorn_batched(ws, stream=None):
     _check(load().uot_sinkhorn_batched(ws.data_ptr(), _stream(stream)), "uot_sinkhorn_batched")
+
+
+def uot_batched_placement(ws, nprob: int) -> list:
+    """Per prepared problem: its on-chip cluster size, or 0 if it streams."""
+    out = (_I32 * nprob)()
+    k = load().uot_batched_placement(ws.data_ptr(), nprob, out)
+    if k < 0:
+        raise UotError(UOT_ERR_INVALID_ARG, "uot_batched_placement")
+    return list(out)[:min(k, nprob)]
 
 
 def uot_batched_results(ws, nprob: int, stream=None, check_status: bool = True):

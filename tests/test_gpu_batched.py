@@ -1,5 +1,6 @@
-"""Batched persistent iteration (uot_sinkhorn_batched) against the FP64 oracle,
-problem by problem, at the FP32 tolerance (1e-5 relative per plan entry)."""
+"""Batched iteration (uot_sinkhorn_batched: on-chip cluster solves and the
+streaming team engine) against the FP64 oracle, problem by problem, at the
+FP32 tolerance (1e-5 relative per plan entry)."""
 
 import math
 
@@ -58,17 +59,64 @@ def check_batch(uot, problems, tuning=None):
 
 
 def test_mixed_batch_matches_oracle(uot):
-    check_batch(uot, mixed_problems())
+    """Default schedule: problems that fit on chip run there (clusters of 1 to
+    16 CTAs), the rest stream."""
+    B = check_batch(uot, mixed_problems())
+    place = B.placement()
+    assert set(place) - {0} and 0 in place, place
+
+
+def test_streaming_engine_only(uot):
+    B = check_batch(uot, mixed_problems(), uot.batch_tuning(resident_max_cluster=0))
+    assert set(B.placement()) == {0}
 
 
 def test_large_teams_on_small_problems(uot):
     """Tiny target work per CTA forces multi-CTA teams (software barriers,
     shared row counters) even for small problems."""
-    check_batch(uot, mixed_problems(), uot.batch_tuning(stages=3, max_team=64, target_elems=1e4))
+    check_batch(uot, mixed_problems(), uot.batch_tuning(stages=3, max_team=64, target_elems=1e4,
+                                                        resident_max_cluster=0))
 
 
 def test_single_cta_teams_only(uot):
-    check_batch(uot, mixed_problems()[:8], uot.batch_tuning(stages=8, max_team=1, target_elems=1e12))
+    check_batch(uot, mixed_problems()[:8], uot.batch_tuning(stages=8, max_team=1, target_elems=1e12,
+                                                            resident_max_cluster=0))
+
+
+def on_chip_problems():
+    """Shapes that need clusters of 1, 2, 4, 8 and 16 CTAs (shared memory of
+    about 227 KB per CTA), with ragged widths, narrow and wide rows (one to
+    256 threads per row) and unequal masses."""
+    shapes = [(1, 1), (3, 5), (7, 4096), (200, 200), (64, 65), (300, 250), (90, 1025),
+              (700, 300), (129, 2049), (1500, 250), (33, 4095), (2000, 300), (4000, 129),
+              (450, 1023)]
+    out = []
+    rng = np.random.default_rng(11)
+    for k, (n, m) in enumerate(shapes):
+        reg = float(rng.uniform(0.03, 0.2))
+        reg_m = math.inf if k % 4 == 3 else float(np.exp(rng.uniform(np.log(0.1), np.log(10))))
+        iters = [0, 3, 30, 12][k % 4]
+        out.append(workloads.uniform2d(seed=300 + k, n=n, m=m, reg=reg, reg_m=reg_m, iters=iters))
+    return out
+
+
+@pytest.mark.parametrize("max_cluster", [1, 2, 4, 8, 16])
+def test_on_chip_cluster_sizes(uot, max_cluster):
+    """Each cap on the cluster size: problems that fit run on chip in the
+    smallest cluster that holds them, the others stream; all match."""
+    B = check_batch(uot, on_chip_problems(), uot.batch_tuning(resident_max_cluster=max_cluster))
+    place = B.placement()
+    assert max(place) <= max_cluster and max_cluster in place, place
+    # The smallest power-of-two cluster whose shared memory (at most 227 KB
+    # per CTA) holds the rows, of padded width, beside the column arrays.
+    for p, c in zip(on_chip_problems(), place):
+        n, m = p.C.shape
+        ldk = (m + 3) // 4 * 4
+        block = lambda cs: 4 * -(-n // cs) * ldk
+        if c:
+            assert block(c) <= 232448 and (c == 1 or block(c // 2) > 160 * 1024), (n, m, c)
+        else:
+            assert block(max_cluster) > 160 * 1024, (n, m)
 
 
 def test_batched_run_captured_in_graph(uot):
