@@ -321,7 +321,7 @@ typedef struct uot_problem {
 } uot_problem;
 
 /* Schedule knobs (uot_batch_default_tuning fills the defaults):
- *   stages        ring depth per streaming CTA (2..8 slots of 16 KB);
+ *   stages        ring depth per streaming CTA (2..6 slots of 32 KB);
  *   max_team      largest streaming team size (a power of two);
  *   target_elems  element-iterations per CTA used to size the teams: a
  *                 problem of N*M*(iters+1) element-iterations gets the

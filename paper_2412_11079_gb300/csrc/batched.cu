@@ -1,12 +1,12 @@
-// Batched Sinkhorn-UOT: many independent problems of uneven size in one
-// persistent launch (the rule of Section 2.1 with Algorithm 1's single sweep
-// per iteration).  Each problem runs in kernel form: during the iterations
-// the plan buffer holds the initial plan K read-only and only the FP32
-// scalings change (plan = diag(U) K diag(V)); the final sweep writes the plan
-// over K.  Compared with rescaling the plan in place this reads 4 instead of
-// moving 8 bytes per element per iteration, and no plan entry accumulates
-// two roundings per iteration (in-place FP32 drifts past 1e-5 on slowly
-// mixing problems after a few hundred iterations).
+// Batched Sinkhorn-UOT, streaming form: many independent problems of uneven
+// size in one persistent launch (the rule of Section 2.1 with Algorithm 1's
+// single sweep per iteration).  Each problem runs in kernel form: during the
+// iterations the plan buffer holds the initial plan K read-only and only the
+// FP32 scalings change (plan = diag(U) K diag(V)); the final sweep writes
+// the plan over K.  Compared with rescaling the plan in place this reads 4
+// instead of moving 8 bytes per element per iteration, and no plan entry
+// accumulates two roundings per iteration.  (Problems small enough for the
+// shared memory of a cluster run in the on-chip engine instead.)
 //
 // Scheduling.  Problems are sorted into size classes; class c is served by
 // teams of G_c CTAs (G_c a power of two, larger for larger problems).  Teams
@@ -18,16 +18,20 @@
 // the next class.  The host picks the classes (the autotuner varies the
 // target work per CTA and the ring depth).
 //
-// Per problem.  The team's CTAs take rows from a per-iteration counter; a
-// CTA processes R = 256 / GT rows per step, GT threads per row (GT the
-// smallest power of two with GT * 16 >= M), so narrow problems keep all
-// threads busy.  Rows arrive through a ring of shared-memory slots filled by
-// 1-D bulk copies.  Each thread holds the column scalings and column partial
-// sums of its 16 columns in registers; partial sums of the row groups are
-// combined in shared memory and folded into the problem's column sums with
-// vector reductions once per iteration, after which the team meets at a
-// software barrier (bounded spin) and every thread updates the scalings of
-// its own columns.  The final sweep writes diag(U) K diag(V).
+// Per problem.  CTA r of a team owns the contiguous rows [r nb, (r+1) nb),
+// nb = ceil(N / G), for all iterations, and keeps their scalings U and
+// marginals a in shared memory.  Each step moves 2R rows (R = 256 / GT row
+// groups of GT threads, GT the smallest power of two with 16 GT >= M; at most
+// 32 KB) into a ring slot with 1-D bulk copies issued by one warp; each
+// thread covers 4 16-byte chunks of two rows, holding its columns' scalings V
+// and column partial sums in registers.  A step: partial row sums (shuffles,
+// one partial per warp), barrier, one thread per row forms the row factor
+// (one power per row rather than one per thread), barrier, column partials
+// of U_i K_ij.  Once per iteration the row groups'
+// partials are combined in shared memory and folded into the problem's
+// column sums with vector reductions, the team meets at a software barrier
+// (bounded spin), and the CTA updates V for all columns (one thread per
+// column).  The final sweep writes diag(U) K diag(V).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,7 +45,6 @@
 #include "uot_internal.h"
 
 namespace uot {
-
 namespace {
 
 constexpr int BT = 256;           // threads per CTA
@@ -50,8 +53,9 @@ constexpr int BW = BT * BKV * 4;  // widest row (FP32 columns)
 constexpr int MAX_CLASSES = 8;
 constexpr int MAX_RES_CLASSES = 5;  // on-chip cluster sizes 1, 2, 4, 8, 16
 constexpr int CURSORS = MAX_CLASSES + MAX_RES_CLASSES;
-constexpr int MAX_STAGES = 8;
-constexpr int SLOT_BYTES = BT * BKV * 16;
+constexpr int MAX_STAGES = 6;
+constexpr int SLOT_BYTES = 2 * BT * BKV * 16;  // two rows per row group
+constexpr int ROWS_MAX = 1024;                 // rows one CTA owns
 
 struct BatchSched {
   int nprob;
@@ -65,7 +69,7 @@ struct BatchSched {
   const int* order;      // problem indices, by class, largest first
   int* cursor;           // [MAX_CLASSES] queue positions
   int* mailbox;          // [teams] problem handed to the team
-  int* bar;              // [teams][2] barrier count, generation
+  int* bar;              // [teams][2] barrier arrival count, unused
 };
 
 struct BatchHeader {  // at the start of the batched workspace (for inspection)
@@ -75,54 +79,57 @@ struct BatchHeader {  // at the start of the batched workspace (for inspection)
   int64_t total;
 };
 
-// Team barrier over G CTAs (G > 1): arrival counter + generation, bounded.
-__device__ bool team_barrier(int* bar, int G, uint32_t& st) {
+// Team barrier over G CTAs (G > 1), bounded: one monotonic arrival counter
+// per team; the e-th barrier of a team completes when the counter reaches
+// e * G.  The release reduction publishes the CTA's earlier writes (ordered
+// before it by the CTA barrier), the acquire loads see the other CTAs'.
+__device__ bool team_barrier(int* count, int G, int& epoch, uint32_t& st) {
   __syncthreads();
   bool ok = true;
+  ++epoch;
   if (threadIdx.x == 0) {
-    int* count = bar;
-    int* gen = bar + 1;
-    const int g0 = ld_acquire_gpu(gen);
-    __threadfence();
-    if (atomicAdd(count, 1) == G - 1) {
-      *count = 0;
-      __threadfence();
-      atomicAdd(gen, 1);
-    } else {
-      const uint64_t t0 = global_timer_ns();
-      while (ld_acquire_gpu(gen) == g0) {
-        if (global_timer_ns() - t0 > WAIT_LIMIT_NS) {
-          st |= DEV_TIMEOUT;
-          ok = false;
-          break;
-        }
+    const int target = epoch * G;
+    red_release_gpu_add(count, 1);
+    const uint64_t t0 = global_timer_ns();
+    while (ld_acquire_gpu(count) < target) {
+      if (global_timer_ns() - t0 > WAIT_LIMIT_NS) {
+        st |= DEV_TIMEOUT;
+        ok = false;
+        break;
       }
     }
   }
   return __syncthreads_and(ok ? 1 : 0) != 0;
 }
 
-// One sweep over the rows of problem P taken by this CTA.  The plan buffer
-// holds K (the initial plan) during the iterations; the scalings are U (per
-// row, in global memory) and V (per column, in registers: V below).
-// Iteration sweep: r_i = U_i sum_j K_ij V_j, U_i <- U_i alpha_i gauge, column
-// partials of U_i K_ij into c_next.  Final sweep: P_ij = (K_ij V_j) U_i
-// written over K.
+__device__ __forceinline__ float4 lds4(const void* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+
+// One sweep over this CTA's rows [r0, r0 + nloc) of problem P.  The plan
+// buffer holds K during the iterations; U (Us) and a (As) of the rows are in
+// shared memory, V in registers.  Iteration sweep: r_i = U_i sum_j K_ij V_j,
+// U_i <- U_i alpha_i gauge, column partials of U_i K_ij into c_next.  Final
+// sweep: P_ij = (K_ij V_j) U_i written over K.
 __device__ void sweep(const BatchProblem& P, bool finish, const float (&V)[BKV][4], float gauge,
-                      int* ctr, float* c_next, int stages, unsigned char* ring, uint64_t* full,
-                      int* slot_rows, float* scratch, int& qbase, uint32_t& st, bool& broken) {
-  const int tid = threadIdx.x;
-  const int m = P.m, n = P.n;
-  const int c4 = (m + 3) / 4;  // 16-byte chunks per row
+                      int r0, int nloc, float* c_next, float* Us, const float* As, int stages,
+                      unsigned char* ring, uint64_t* full, float* rp, float* uf, int& qbase,
+                      uint32_t& st, bool& broken) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = P.m;
+  const int ldk = (m + 3) & ~3, c4 = ldk >> 2;
   int gt = 1;
   while (gt * BKV < c4) gt <<= 1;  // threads per row
-  const int R = BT / gt;           // rows per step
-  const int g = tid / gt, l = tid % gt;
-  const int row_stride = gt * BKV * 16;  // bytes per row in a slot
-  const uint32_t row_bytes = uint32_t((size_t(m) * 4) & ~size_t(15));
+  const int R = BT / gt, RS = 2 * R;
+  const int g = tid / gt, l = tid - g * gt;
+  const int wr = gt < 32 ? gt : 32;  // lanes of one row within a warp
+  const int wpg = gt > 32 ? gt >> 5 : 1;  // warps per row group
+  const int wg = warp % wpg;              // this warp's place in its group
+  const uint32_t row_bytes = uint32_t(ldk) * 4;  // 16-byte multiple; padding lies in ldp
+  const int nsteps = (nloc + RS - 1) / RS;
   const int64_t ldp = P.ldp;
   float* plan = P.plan;
-  const uint64_t policy = policy_evict_first();
+  const float fi = P.fi;
 
   float cacc[BKV][4];
 #pragma unroll
@@ -130,182 +137,199 @@ __device__ void sweep(const BatchProblem& P, bool finish, const float (&V)[BKV][
 #pragma unroll
     for (int e = 0; e < 4; ++e) cacc[k][e] = 0.0f;
 
-  __syncthreads();  // the ring is free (previous sweep finished with it)
-  // Steps are numbered across sweeps (qbase) so the mbarrier phases continue;
-  // every sweep consumes exactly the steps it arms.  Thread 0 takes row
-  // blocks one step ahead so it never waits on the counter.
-  int issued = qbase;
-  int next_base = 0;
-  if (tid == 0) next_base = atomicAdd(ctr, R);
-  auto arm = [&](int q) {
-    const int slot = q % stages;
-    const int base = next_base;
-    if (base < n) next_base = atomicAdd(ctr, R);
-    uint32_t bytes = 0;
-    for (int r = 0; r < R; ++r) {
-      const int row = base + r;
-      const bool ok = row < n;
-      slot_rows[slot * BT + r] = ok ? row : -1;
-      if (ok) bytes += row_bytes;
-    }
-    if (base >= n) {
-      mbar_arrive(&full[slot]);
-      return false;
-    }
-    if (bytes) {
-      mbar_arrive_expect_tx(&full[slot], bytes);
-      for (int r = 0; r < R && base + r < n; ++r)
-        bulk_load(ring + size_t(slot) * SLOT_BYTES + size_t(r) * row_stride,
-                  plan + int64_t(base + r) * ldp, row_bytes, &full[slot], policy);
-    } else {
-      mbar_arrive(&full[slot]);
-    }
-    return true;
+  // The ring was last written through the generic proxy (column sums, V);
+  // order that before the bulk copies that refill it.
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  // Warp 0 fills ring slots: one expect-tx arrival, then a bulk copy per row
+  // spread over the lanes.  Steps are numbered across sweeps (qbase) so the
+  // mbarrier phases continue.
+  const uint64_t policy = policy_evict_normal();
+  auto arm = [&](int ql) {
+    const int slot = (qbase + ql) % stages;
+    const int rb = ql * RS;
+    const int rows = min(RS, nloc - rb);
+    if (lane == 0) mbar_arrive_expect_tx(&full[slot], uint32_t(rows) * row_bytes);
+    __syncwarp();
+    for (int r = lane; r < rows; r += 32)
+      bulk_load(ring + size_t(slot) * SLOT_BYTES + size_t(r) * row_bytes,
+                plan + int64_t(r0 + rb + r) * ldp, row_bytes, &full[slot], policy);
   };
-  bool more = true;
-  if (tid == 0) {
-    // Rows were written through the generic proxy in the previous sweep
-    // (by this team, within this launch); order those writes before the
-    // bulk copies (async proxy) that read them back.
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    for (int q = 0; q < stages && more; ++q) {
-      more = arm(qbase + q);
-      ++issued;
-    }
-  }
-  // U_i and a_i of the next step's rows, loaded one step ahead so that their
-  // latency overlaps this step.
-  float u_pf = 0.0f, a_pf = 0.0f;
-  bool have_pf = false;
-  int q = qbase;
-  for (;; ++q) {
+  int armed = min(stages, nsteps);
+  if (warp == 0)
+    for (int ql = 0; ql < armed; ++ql) arm(ql);
+
+  const bool ragged = (m & 3) != 0;
+  int ql = 0;
+  for (; ql < nsteps; ++ql) {
+    const int q = qbase + ql;
     const int slot = q % stages;
     if (!broken && !mbar_wait_bounded(&full[slot], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS)) {
       broken = true;
       st |= DEV_TIMEOUT;
     }
-    const int row0 = *reinterpret_cast<volatile int*>(&slot_rows[slot * BT]);
-    if (row0 < 0) {  // uniform: rows are taken in blocks, first row decides
-      ++q;
-      break;
-    }
-    const int row = *reinterpret_cast<volatile int*>(&slot_rows[slot * BT + g]);
-    const bool live = row >= 0;
-    const unsigned char* srow = ring + size_t(slot) * SLOT_BYTES + size_t(g) * row_stride;
-    float* grow = plan + int64_t(live ? row : 0) * ldp;
-    float x[BKV][4];
-    float s = 0.0f;
-    float u_old = 0.0f, a_row = 0.0f;
-    if (have_pf) {
-      u_old = u_pf;
-      a_row = a_pf;
-    } else if (live) {
-      u_old = __ldcg(P.U + row);
-      if (!finish) a_row = __ldg(P.a + row);
-    }
+    const int ia = ql * RS + g, ib = ia + R;  // local rows of this group
+    const bool la = ia < nloc, lb = ib < nloc;
+    const unsigned char* sa_ = ring + size_t(slot) * SLOT_BYTES + size_t(g) * row_bytes;
+    const unsigned char* sb_ = sa_ + size_t(R) * row_bytes;
+    float xa[BKV][4], xb[BKV][4];
+    float pa = 0.0f, pb = 0.0f;
 #pragma unroll
     for (int k = 0; k < BKV; ++k) {
       const int ch = l + k * gt;
-      const int cc = ch * 4;
-      if (live && cc + 4 <= m) {
-        Elem<float>::unpack(ld_shared_v4(srow + size_t(ch) * 16), x[k]);
-      } else {
+      const bool cv = ch < c4;
+      const float4 va = (cv && la) ? lds4(sa_ + size_t(ch) * 16) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 vb = (cv && lb) ? lds4(sb_ + size_t(ch) * 16) : make_float4(0.f, 0.f, 0.f, 0.f);
+      xa[k][0] = va.x; xa[k][1] = va.y; xa[k][2] = va.z; xa[k][3] = va.w;
+      xb[k][0] = vb.x; xb[k][1] = vb.y; xb[k][2] = vb.z; xb[k][3] = vb.w;
+      if (ragged && ch == c4 - 1) {  // the copy ran past column m - 1 into padding
 #pragma unroll
-        for (int e = 0; e < 4; ++e) x[k][e] = (live && cc + e < m) ? grow[cc + e] : 0.0f;
+        for (int e = 1; e < 4; ++e)
+          if (ch * 4 + e >= m) {
+            xa[k][e] = 0.0f;
+            xb[k][e] = 0.0f;
+          }
       }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) s = fmaf(x[k][e], V[k][e], s);
+      pa = fmaf(xa[k][3], V[k][3], fmaf(xa[k][2], V[k][2], fmaf(xa[k][1], V[k][1], fmaf(xa[k][0], V[k][0], pa))));
+      pb = fmaf(xb[k][3], V[k][3], fmaf(xb[k][2], V[k][2], fmaf(xb[k][1], V[k][1], fmaf(xb[k][0], V[k][0], pb))));
     }
-    // Row sum over the gt threads of the group: shuffles within the warp,
-    // then shared memory across the group's warps.
-    const int w = min(gt, 32);
-    for (int o = w >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    float* red = scratch + (q & 1) * (BT / 32);
-    if (gt > 32 && (tid & 31) == 0) red[tid >> 5] = s;
-    const int anyb = __syncthreads_or(broken ? 1 : 0);
-    if (anyb) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      if (o < wr) {
+        pa += __shfl_xor_sync(0xffffffffu, pa, o);
+        pb += __shfl_xor_sync(0xffffffffu, pb, o);
+      }
+    }
+    // One partial per warp and row of the step.
+    if ((lane & (wr - 1)) == 0) {
+      rp[g * wpg + wg] = pa;
+      rp[(g + R) * wpg + wg] = pb;
+    }
+    if (__syncthreads_or(broken ? 1 : 0)) {
       broken = true;
       st |= DEV_TIMEOUT;
       break;
     }
-    {
-      // Step q + 1 was armed at step q + 1 - stages (or before the loop),
-      // ahead of this barrier; its slot is re-armed only after the next one.
-      const int nrow = *reinterpret_cast<volatile int*>(&slot_rows[((q + 1) % stages) * BT + g]);
-      have_pf = true;
-      u_pf = nrow >= 0 ? __ldcg(P.U + nrow) : 0.0f;
-      a_pf = (nrow >= 0 && !finish) ? __ldg(P.a + nrow) : 0.0f;
+    // Every thread holds this slot's rows in registers: refill it.  Every
+    // thread counts the armed steps (the phase bookkeeping of later sweeps).
+    if (ql + stages < nsteps) {
+      if (warp == 0) arm(ql + stages);
+      ++armed;
     }
-    if (tid == 0 && more) {
-      more = arm(issued);
-      ++issued;
+    // Row factors, one thread per row of the step: U_i <- U_i alpha_i gauge
+    // with r_i = U_i sum_j K_ij V_j (the final sweep only reads U_i).
+    for (int r = tid; r < RS; r += BT) {
+      const int i = ql * RS + r;
+      if (i < nloc) {
+        const float u_old = Us[i];
+        if (finish) {
+          uf[r] = u_old;
+        } else {
+          float sum = 0.0f;
+          for (int w = 0; w < wpg; ++w) sum += rp[r * wpg + w];
+          const float u_new = u_old * rescale_factor(As[i], u_old * sum, fi, st) * gauge;
+          Us[i] = u_new;
+          uf[r] = u_new;
+        }
+      }
     }
-    if (gt > 32) {
-      const int wpg = gt / 32, w0 = (g * gt) / 32;
-      s = 0.0f;
-      for (int k = 0; k < wpg; ++k) s += red[w0 + k];
-    }
-    if (!live) continue;
+    __syncthreads();
+    const float fa = la ? uf[g] : 0.0f, fb = lb ? uf[g + R] : 0.0f;
     if (finish) {
 #pragma unroll
-      for (int k = 0; k < BKV; ++k) {
-        const int cc = (l + k * gt) * 4;
-        float y[4];
+      for (int h = 0; h < 2; ++h) {
+        const bool live = h == 0 ? la : lb;
+        if (!live) continue;
+        const float u = h == 0 ? fa : fb;
+        float* grow = plan + int64_t(r0 + (h == 0 ? ia : ib)) * ldp;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) y[e] = (x[k][e] * V[k][e]) * u_old;
-        if (cc + 4 <= m) {
-          st_global_cs_v4(grow + cc, Elem<float>::pack(y));
-        } else {
+        for (int k = 0; k < BKV; ++k) {
+          const int cc = (l + k * gt) * 4;
+          if (cc >= m) continue;
+          float y[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (cc + e < m) grow[cc + e] = y[e];
+          for (int e = 0; e < 4; ++e) y[e] = ((h == 0 ? xa[k][e] : xb[k][e]) * V[k][e]) * u;
+          if (cc + 4 <= m) {
+            st_global_cs_v4(grow + cc, Elem<float>::pack(y));
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (cc + e < m) grow[cc + e] = y[e];
+          }
         }
       }
       continue;
     }
-    const float u_new = u_old * rescale_factor(a_row, u_old * s, P.fi, st) * gauge;
-    if (l == 0) P.U[row] = u_new;
 #pragma unroll
     for (int k = 0; k < BKV; ++k)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) cacc[k][e] = fmaf(u_new, x[k][e], cacc[k][e]);
+      for (int e = 0; e < 4; ++e) cacc[k][e] = fmaf(fb, xb[k][e], fmaf(fa, xa[k][e], cacc[k][e]));
   }
-  qbase = q;
-  // Writer side of the same ordering: every thread's stores of this sweep
-  // before any later bulk copy of these rows (after the barriers that follow).
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-  if (finish) return;
-  // Combine the row groups' column partials (groups own the same columns)
-  // in the now idle ring, then fold them into the column sums.
+  if (broken) {
+    // Copies of abandoned steps: wait for them (bounded) before the ring
+    // may be reused or the CTA exits.
+    for (int q2 = qbase + ql; q2 < qbase + armed; ++q2)
+      mbar_wait_bounded(&full[q2 % stages], uint32_t(q2 / stages) & 1u, WAIT_LIMIT_NS);
+  }
+  qbase += armed;
+  if (finish || broken) return;
+  // Combine the R row groups' column partials (they cover the same columns)
+  // in the idle ring: groups [R/2, R) hand theirs to groups [0, R/2), then
+  // one thread per 4 columns sums the R/2 pair sums into the column sums.
   __syncthreads();
-  float* acc = reinterpret_cast<float*>(ring);  // c4 * 4 floats
-  for (int j = tid; j < c4 * 4; j += BT) acc[j] = 0.0f;
-  __syncthreads();
-  for (int gg = 0; gg < R; ++gg) {
-    if (g == gg) {
+  float* W = reinterpret_cast<float*>(ring);
+  const int half = R / 2;
+  if (half == 0) {
+#pragma unroll
+    for (int k = 0; k < BKV; ++k) {
+      const int ch = l + k * gt;
+      if (ch < c4)
+        *reinterpret_cast<float4*>(W + ch * 4) =
+            make_float4(cacc[k][0], cacc[k][1], cacc[k][2], cacc[k][3]);
+    }
+  } else {
+    if (g >= half) {
 #pragma unroll
       for (int k = 0; k < BKV; ++k) {
         const int ch = l + k * gt;
         if (ch < c4)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc[ch * 4 + e] += cacc[k][e];
+          *reinterpret_cast<float4*>(W + size_t(g - half) * ldk + ch * 4) =
+              make_float4(cacc[k][0], cacc[k][1], cacc[k][2], cacc[k][3]);
       }
     }
     __syncthreads();
-  }
-  for (int ch = tid; ch < c4; ch += BT) {
-    const int cc = ch * 4;
-    if (cc + 4 <= m) {
-      red_add_v4(c_next + cc, acc[cc], acc[cc + 1], acc[cc + 2], acc[cc + 3]);
-    } else {
-      for (int e = 0; e < 4; ++e)
-        if (cc + e < m) atomicAdd(c_next + cc + e, acc[cc + e]);
+    if (g < half) {
+#pragma unroll
+      for (int k = 0; k < BKV; ++k) {
+        const int ch = l + k * gt;
+        if (ch < c4) {
+          float4* w = reinterpret_cast<float4*>(W + size_t(g) * ldk + ch * 4);
+          const float4 o = *w;
+          *w = make_float4(cacc[k][0] + o.x, cacc[k][1] + o.y, cacc[k][2] + o.z, cacc[k][3] + o.w);
+        }
+      }
     }
   }
-  // The ring was written through the generic proxy; order that before the
-  // next bulk copies into it.
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
+  const int copies = half > 0 ? half : 1;
+  for (int ch = tid; ch < c4; ch += BT) {
+    float4 s4 = lds4(W + ch * 4);
+    for (int u = 1; u < copies; ++u) {
+      const float4 o = lds4(W + size_t(u) * ldk + ch * 4);
+      s4.x += o.x;
+      s4.y += o.y;
+      s4.z += o.z;
+      s4.w += o.w;
+    }
+    const int cc = ch * 4;
+    if (cc + 4 <= m) {
+      red_add_v4(c_next + cc, s4.x, s4.y, s4.z, s4.w);
+    } else {
+      const float v4[4] = {s4.x, s4.y, s4.z, s4.w};
+      for (int e = 0; e < 4; ++e)
+        if (cc + e < m) atomicAdd(c_next + cc + e, v4[e]);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(BT, 2) batched_kernel(const BatchSched S) {
@@ -313,8 +337,10 @@ __global__ void __launch_bounds__(BT, 2) batched_kernel(const BatchSched S) {
   const int stages = S.stages;
   unsigned char* ring = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(stages) * SLOT_BYTES);
-  int* slot_rows = reinterpret_cast<int*>(full + MAX_STAGES);
-  float* scratch = reinterpret_cast<float*>(slot_rows + MAX_STAGES * BT);
+  float* Us = reinterpret_cast<float*>(full + MAX_STAGES);
+  float* As = Us + ROWS_MAX;
+  float* rp = As + ROWS_MAX;  // row-sum partials of a step (rows x warps per row)
+  float* uf = rp + 2 * BT;    // row factors of a step
   __shared__ int s_prob;
   const int tid = threadIdx.x;
   uint32_t st = 0;
@@ -334,6 +360,7 @@ __global__ void __launch_bounds__(BT, 2) batched_kernel(const BatchSched S) {
     if ((team + 1) * G > int(gridDim.x)) continue;  // incomplete team
     const int rank = blockIdx.x % G;
     int* bar = S.bar + 2 * (S.team_base[c] + team);
+    int epoch = 0;  // barriers of this team passed so far
     int* mbox = S.mailbox + S.team_base[c] + team;
     while (true) {
       // The leader takes the next problem of this class and hands it over.
@@ -344,58 +371,97 @@ __global__ void __launch_bounds__(BT, 2) batched_kernel(const BatchSched S) {
         s_prob = idx;
       }
       if (G > 1) {
-        if (!team_barrier(bar, G, st)) { broken = true; break; }
+        if (!team_barrier(bar, G, epoch, st)) { broken = true; break; }
         if (tid == 0) s_prob = ld_acquire_gpu(mbox);
       }
       __syncthreads();
       const int pi = s_prob;
       if (pi < 0) break;
       const BatchProblem P = S.probs[pi];
-      const int c4 = (P.m + 3) / 4;
-      // Column scalings V of this thread's columns, in registers: every row
-      // group (and every CTA of the team) computes the same values.
-      float V[BKV][4];
+      const int m = P.m;
+      const int ldk = (m + 3) & ~3, c4 = ldk >> 2;
       int gt = 1;
       while (gt * BKV < c4) gt <<= 1;
       const int l = tid % gt;
+      // This CTA's rows, their scalings and marginals.
+      const int nb = (P.n + G - 1) / G;
+      const int r0 = min(P.n, rank * nb);
+      const int nloc = max(0, min(P.n - r0, nb));
+      for (int i = tid; i < nloc; i += BT) {
+        Us[i] = 1.0f;
+        As[i] = __ldg(P.a + r0 + i);
+      }
+      // Column scalings V of this thread's columns, in registers (every row
+      // group and every CTA of the team holds the same values).
+      float V[BKV][4];
 #pragma unroll
       for (int k = 0; k < BKV; ++k)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) V[k][e] = ((l + k * gt) * 4 + e < P.m) ? 1.0f : 0.0f;
-      // The scalings drift as U ~ k^t, V ~ k^-t (row factors tend to k at the
-      // fixed point); an exact power of two moves between them every pass.
+        for (int e = 0; e < 4; ++e) V[k][e] = ((l + k * gt) * 4 + e < m) ? 1.0f : 0.0f;
       const float Lf = float(*P.log2k);
       float gauge = 1.0f, inv_gauge = 1.0f;
       for (int t = 1; t <= P.iters + 1 && !broken; ++t) {
         const bool finish = t == P.iters + 1;
-        // V_j <- V_j (b_j / c_j)^fi 2^-e_{t-1}, c_j = V_j 2^-e_{t-1} sum_i U_i K_ij.
         if (t > 1) {
+          // V_j <- V_j (b_j / c_j)^fi 2^-e_{t-1}, c_j = V_j 2^-e_{t-1} sum_i U_i K_ij:
+          // one thread per column, through the idle ring.
+          float* Vsm = reinterpret_cast<float*>(ring);
+          if (tid < gt) {
 #pragma unroll
-          for (int k = 0; k < BKV; ++k)
+            for (int k = 0; k < BKV; ++k) {
+              const int ch = l + k * gt;
+              if (ch < c4)
+                *reinterpret_cast<float4*>(Vsm + ch * 4) = make_float4(V[k][0], V[k][1], V[k][2], V[k][3]);
+            }
+          }
+          __syncthreads();
+          const float* cprev = P.c + size_t((t - 1) % 3) * P.mpad;
+          constexpr int VB = 8;  // columns per thread in flight
+          for (int j0 = tid; j0 < m; j0 += VB * BT) {
+            float cv[VB], bv[VB];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int j = (l + k * gt) * 4 + e;
-              if (j < P.m) {
-                const float cj = V[k][e] * __ldcg(P.c + size_t((t - 1) % 3) * P.mpad + j) * inv_gauge;
-                V[k][e] = V[k][e] * rescale_factor(__ldg(P.b + j), cj, P.fi, st) * inv_gauge;
+            for (int u = 0; u < VB; ++u) {
+              const int j = j0 + u * BT;
+              cv[u] = j < m ? __ldcg(cprev + j) : 0.0f;
+              bv[u] = j < m ? __ldg(P.b + j) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < VB; ++u) {
+              const int j = j0 + u * BT;
+              if (j < m) {
+                const float v = Vsm[j];
+                const float cj = v * cv[u] * inv_gauge;
+                Vsm[j] = v * rescale_factor(bv[u], cj, P.fi, st) * inv_gauge;
               }
             }
+          }
+          __syncthreads();
+#pragma unroll
+          for (int k = 0; k < BKV; ++k) {
+            const int ch = l + k * gt;
+            if (ch < c4) {
+              const float4 v4 = lds4(Vsm + ch * 4);
+              V[k][0] = v4.x;
+              V[k][1] = v4.y;
+              V[k][2] = v4.z;
+              V[k][3] = v4.w;
+            }
+          }
         }
         if (!finish) {
           const int ex = gauge_exponent(t, Lf);
           gauge = ldexpf(1.0f, ex);
           inv_gauge = ldexpf(1.0f, -ex);
         }
-        // Clear the buffers of iteration t + 1 (leader CTA).
+        // Clear the column sums of iteration t + 1 (leader CTA).
         if (rank == 0) {
           float* cl = P.c + size_t((t + 1) % 3) * P.mpad;
           for (int j = tid; j < P.mpad; j += BT) cl[j] = 0.0f;
-          if (tid == 0) P.ctr[(t + 1) % 3] = 0;
         }
-        sweep(P, finish, V, gauge, P.ctr + t % 3, P.c + size_t(t % 3) * P.mpad, stages, ring,
-              full, slot_rows, scratch, qbase, st, broken);
+        sweep(P, finish, V, gauge, r0, nloc, P.c + size_t(t % 3) * P.mpad, Us, As, stages, ring,
+              full, rp, uf, qbase, st, broken);
         if (G > 1) {
-          if (!team_barrier(bar, G, st)) { broken = true; break; }
+          if (!team_barrier(bar, G, epoch, st)) { broken = true; break; }
         } else {
           __syncthreads();
         }
@@ -458,7 +524,7 @@ __global__ void batched_reset_kernel(const BatchProblem* probs, int nprob, int* 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t batched_smem(int stages) {
-  return size_t(stages) * SLOT_BYTES + MAX_STAGES * 8 + MAX_STAGES * BT * 4 + 2 * (BT / 32) * 4;
+  return size_t(stages) * SLOT_BYTES + MAX_STAGES * 8 + 2 * ROWS_MAX * 4 + 2 * (2 * BT) * 4;
 }
 
 }  // namespace
@@ -598,10 +664,14 @@ uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uo
     if (rescls[i] >= 0) continue;
     int g = 1;
     while (g < tu.max_team && g * 2 <= grid && double(g) * tu.target_elems < work[i]) g <<= 1;
+    // A CTA keeps the scalings of at most ROWS_MAX rows.
+    while (g < grid && int64_t(g) * ROWS_MAX < probs[i].n) g <<= 1;
+    if (int64_t(g) * ROWS_MAX < probs[i].n || g > grid) return UOT_ERR_UNSUPPORTED;
     gsize[i] = g;
   }
   std::vector<int> classes;
-  for (int g = tu.max_team; g >= 1; g >>= 1)
+  const int gmax = nprob > 0 ? *std::max_element(gsize.begin(), gsize.end()) : 1;
+  for (int g = gmax; g >= 1; g >>= 1)
     for (int i = 0; i < nprob; ++i)
       if (gsize[i] == g) {
         classes.push_back(g);

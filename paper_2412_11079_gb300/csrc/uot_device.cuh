@@ -79,16 +79,15 @@ template <> struct Elem<__half> {
 // ------------------------------------------------------------ the factor
 // (target / total)^fi of Section 2.1 with the degenerate readings:
 // target == 0 -> 0; total == 0 < target -> 1 (ZERO_SUM); non-finite -> flag.
+// Written without branches around the power so that several factors can be
+// evaluated side by side.
 __device__ __forceinline__ float rescale_factor(float target, float total, float fi,
                                                 uint32_t& st) {
-  if (target == 0.0f) return 0.0f;
-  if (total == 0.0f) {
-    st |= DEV_ZERO_SUM;
-    return 1.0f;
-  }
-  const float f = powf(target / total, fi);
-  if (!isfinite(f) || !isfinite(total)) st |= DEV_NONFINITE;
-  return f;
+  const bool tz = target == 0.0f, sz = total == 0.0f;
+  const float f = powf(tz || sz ? 1.0f : target / total, fi);
+  st |= (!tz && sz) ? DEV_ZERO_SUM : 0u;
+  st |= (!tz && !sz && (!isfinite(f) || !isfinite(total))) ? DEV_NONFINITE : 0u;
+  return tz ? 0.0f : (sz ? 1.0f : f);
 }
 
 // Exponent of the kernel form's power-of-two gauge at iteration t,
@@ -165,6 +164,12 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       : "memory");
 }
 
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -191,6 +196,10 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
                "f"(d)
                : "memory");
+}
+
+__device__ __forceinline__ void red_release_gpu_add(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {

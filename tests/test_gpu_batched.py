@@ -79,7 +79,7 @@ def test_large_teams_on_small_problems(uot):
 
 
 def test_single_cta_teams_only(uot):
-    check_batch(uot, mixed_problems()[:8], uot.batch_tuning(stages=8, max_team=1, target_elems=1e12,
+    check_batch(uot, mixed_problems()[:8], uot.batch_tuning(stages=6, max_team=1, target_elems=1e12,
                                                             resident_max_cluster=0))
 
 
