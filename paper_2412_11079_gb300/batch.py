@@ -17,14 +17,16 @@ _TUNE_CACHE: dict = {}
 
 
 class Batch:
-    def __init__(self, problems, device=None):
-        """problems: objects with C (N x M float32 numpy), a, b, reg, reg_m, iters."""
+    def __init__(self, problems, device=None, pad: int = 0):
+        """problems: objects with C (N x M float32 numpy), a, b, reg, reg_m, iters.
+        pad: extra elements per row beyond the 16-byte rounding (a multiple
+        of 4), for plans that are views into wider storage."""
         self.device = torch.device(device or "cuda")
         self.problems = problems
         self.C, self.plans, self.stores, self.a, self.b = [], [], [], [], []
         for p in problems:
             n, m = p.C.shape
-            ld = (m + 3) // 4 * 4
+            ld = (m + 3) // 4 * 4 + pad
             store = torch.zeros((n, ld), dtype=torch.float32, device=self.device)
             self.stores.append(store)
             self.plans.append(store[:, :m])

@@ -45,6 +45,7 @@
 #include "uot_internal.h"
 
 namespace uot {
+
 namespace {
 
 constexpr int BT = 256;           // threads per CTA
@@ -145,15 +146,26 @@ __device__ void sweep(const BatchProblem& P, bool finish, const float (&V)[BKV][
   // spread over the lanes.  Steps are numbered across sweeps (qbase) so the
   // mbarrier phases continue.
   const uint64_t policy = policy_evict_normal();
+  // Rows stored without padding beyond the 16-byte rounding are contiguous:
+  // one copy per step.
+  const bool packed = ldp == ldk;
   auto arm = [&](int ql) {
     const int slot = (qbase + ql) % stages;
     const int rb = ql * RS;
     const int rows = min(RS, nloc - rb);
+    unsigned char* dst = ring + size_t(slot) * SLOT_BYTES;
+    const float* src = plan + int64_t(r0 + rb) * ldp;
+    if (packed) {
+      if (lane == 0) {
+        mbar_arrive_expect_tx(&full[slot], uint32_t(rows) * row_bytes);
+        bulk_load(dst, src, uint32_t(rows) * row_bytes, &full[slot], policy);
+      }
+      return;
+    }
     if (lane == 0) mbar_arrive_expect_tx(&full[slot], uint32_t(rows) * row_bytes);
     __syncwarp();
     for (int r = lane; r < rows; r += 32)
-      bulk_load(ring + size_t(slot) * SLOT_BYTES + size_t(r) * row_bytes,
-                plan + int64_t(r0 + rb + r) * ldp, row_bytes, &full[slot], policy);
+      bulk_load(dst + size_t(r) * row_bytes, src + int64_t(r) * ldp, row_bytes, &full[slot], policy);
   };
   int armed = min(stages, nsteps);
   if (warp == 0)
@@ -217,8 +229,10 @@ __device__ void sweep(const BatchProblem& P, bool finish, const float (&V)[BKV][
       ++armed;
     }
     // Row factors, one thread per row of the step: U_i <- U_i alpha_i gauge
-    // with r_i = U_i sum_j K_ij V_j (the final sweep only reads U_i).
-    for (int r = tid; r < RS; r += BT) {
+    // with r_i = U_i sum_j K_ij V_j (the final sweep only reads U_i).  The
+    // threads are counted from the last warp, so that warp 0's refill and
+    // the factors' latency overlap.
+    for (int r = BT - 1 - tid; r >= 0 && r < RS; r += BT) {
       const int i = ql * RS + r;
       if (i < nloc) {
         const float u_old = Us[i];

@@ -44,9 +44,9 @@ def mixed_problems():
     return out
 
 
-def check_batch(uot, problems, tuning=None):
+def check_batch(uot, problems, tuning=None, pad=0):
     from paper_2412_11079_gb300.batch import Batch
-    B = Batch(problems)
+    B = Batch(problems, pad=pad)
     B.init_plans()
     B.prepare(tuning)
     B.run()
@@ -69,6 +69,14 @@ def test_mixed_batch_matches_oracle(uot):
 def test_streaming_engine_only(uot):
     B = check_batch(uot, mixed_problems(), uot.batch_tuning(resident_max_cluster=0))
     assert set(B.placement()) == {0}
+
+
+def test_padded_rows_streaming_and_on_chip(uot):
+    """Plans that are views into wider rows (leading dimension beyond the
+    16-byte rounding): per-row copies in the streaming engine, strided loads
+    on chip."""
+    check_batch(uot, mixed_problems(), uot.batch_tuning(resident_max_cluster=0), pad=12)
+    check_batch(uot, mixed_problems(), pad=8)
 
 
 def test_large_teams_on_small_problems(uot):
