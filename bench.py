@@ -39,6 +39,8 @@ sys.path.insert(0, ROOT)
 METRIC = "UOT Sinkhorn plan elems/s & HBM GB/s vs 8 TB/s; fused/bf16/batched vs plain FP32"
 UNIT = "plan elems/s"
 KERNEL_SOURCES = ["paper_2412_11079_gb300/csrc/fused.cu",
+                  "paper_2412_11079_gb300/csrc/fused_kernel.cuh",
+                  "paper_2412_11079_gb300/csrc/fused_inplace.cu",
                   "paper_2412_11079_gb300/csrc/uot_device.cuh",
                   "paper_2412_11079_gb300/csrc/uot_internal.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_pass_traffic.json")
@@ -254,9 +256,14 @@ def run_batched(args):
 
     build.build()
     uot.load()
-    probs = workloads.batch_uneven(seed=0, iters=args.iters)
+    probs = workloads.batch_uneven(seed=0, count=args.nprob, iters=args.iters)
     B = Batch(probs)
-    best, timings = autotune(B)
+    if args.tuning:
+        st_, mt_, te_, rc_ = args.tuning.split(",")
+        best, timings = uot.batch_tuning(int(st_), int(mt_), float(te_), int(rc_)), {}
+        B.prepare(best)
+    else:
+        best, timings = autotune(B)
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
     g = torch.cuda.CUDAGraph()
@@ -306,7 +313,7 @@ def run_batched(args):
             uot.uot_kform_plan(pl, U, V, pl)
 
     loop_ms = {}
-    for name, fn in (("inplace", loop_inplace), ("kform", loop_kform)):
+    for name, fn in () if args.no_compare else (("inplace", loop_inplace), ("kform", loop_kform)):
         fn()
         torch.cuda.synchronize()
         e0.record()
@@ -466,6 +473,11 @@ def main():
     ap.add_argument("--workload", default="large",
                     choices=["large", "precision", "batched", "grad"])
     ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--nprob", type=int, default=512,
+                    help="batched workload: number of problems")
+    ap.add_argument("--tuning", default="",
+                    help="batched workload: fixed schedule stages,max_team,target,cluster "
+                         "(skips the autotuner)")
     ap.add_argument("--grad-check-iters", type=int, default=5)
     ap.add_argument("--grad-streams", type=int, default=8)
     ap.add_argument("--grad-max-ctas", type=int, default=80)
