@@ -335,7 +335,7 @@ def run_batched(args):
         "looped_single_launches": {k: {"ms": v, "elems_per_s": elems / (v * 1e-3)}
                                    for k, v in loop_ms.items()},
         "batched_over_loop": {k: v / ms for k, v in loop_ms.items()},
-        "autotune_ms": {f"{k[0]}/{k[1]}/{k[2]:.0e}": v for k, v in timings.items()},
+        "autotune_ms": {f"{k[0]}/{k[1]}/{k[2]:.0e}/{k[3]}": v for k, v in timings.items()},
     }), flush=True)
 
 

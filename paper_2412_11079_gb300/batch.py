@@ -77,18 +77,21 @@ class Batch:
 
 
 def candidates():
+    """Ring depths that keep two streaming CTAs per SM, team sizes, work per
+    CTA, and the largest on-chip cluster."""
     out = []
-    for stages in (3, 4, 6):
+    for stages in (2, 3):
         for max_team in (16, 32, 64):
-            for target in (1.0e7, 4.0e7, 1.6e8):
-                out.append(uot.batch_tuning(stages, max_team, target))
+            for target in (1.0e7, 4.0e7):
+                for cluster in (8, 16):
+                    out.append(uot.batch_tuning(stages, max_team, target, cluster))
     return out
 
 
 def autotune(batch: Batch, cands=None, repeats: int = 1):
     """Times each candidate schedule on the batch (plans re-initialised before
     every run) and prepares the batch with the fastest.  Returns
-    (best tuning, {(stages, max_team, target): ms})."""
+    (best tuning, {(stages, max_team, target, cluster): ms})."""
     key = batch.key()
     if key in _TUNE_CACHE:
         batch.prepare(_TUNE_CACHE[key])
@@ -107,7 +110,7 @@ def autotune(batch: Batch, cands=None, repeats: int = 1):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         m = min(ms[1:]) if len(ms) > 1 else ms[0]
-        timings[(t.stages, t.max_team, t.target_elems)] = m
+        timings[(t.stages, t.max_team, t.target_elems, t.resident_max_cluster)] = m
         if m < best_ms:
             best, best_ms = t, m
     _TUNE_CACHE[key] = best
