@@ -20,7 +20,7 @@ size_t smem_bytes(const FusedConfig& c, int stages) {
   const size_t row = size_t(c.cols) * elem_size(c.dtype);
   const size_t red = 2 * MAX_CLUSTER * (c.threads / 32) * sizeof(float);
   const size_t slots = size_t(stages > 0 ? stages : 1);
-  return size_t(stages) * row + red + slots * 8 + slots * 4;
+  return size_t(stages) * row + red + slots * 8 + slots * 4 + 2 * sizeof(float);
 }
 
 // cudaFuncSetAttribute is set once per (device, kernel) and the launch

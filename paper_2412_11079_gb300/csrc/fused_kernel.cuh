@@ -126,6 +126,10 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
   const bool dyn = TMA && p.dynamic && cs == 1;
   const int nq = cid < n ? (n - 1 - cid) / ncl + 1 : 0;  // static rows
   int* slot_row = reinterpret_cast<int*>(bars + (TMA ? stages : 1));
+  float* uf = reinterpret_cast<float*>(slot_row + (TMA ? stages : 1));  // [2] row factor
+  // The thread that forms a row's factor in the kernel form: in the last
+  // warp, away from thread 0's refills.
+  constexpr int ftid = KF ? THREADS - 1 : 0;
   uint64_t policy = 0;
   int issued = 0;     // steps whose slot has been armed (thread 0 only)
   int next_row = n;   // dynamic: row index fetched one step ahead (thread 0)
@@ -266,10 +270,14 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
         for (int e = 0; e < VE; ++e) x[k][e] = (cc + e < m) ? E::load1(grow + cc + e) : 0.0f;
       }
     }
-    const float arow = __ldg(p.a + row);
+    // Kernel form: one thread (ftid) forms the row factor; in place, every
+    // thread scales the row and needs a_i.
+    float arow = 0.0f, u_old = 1.0f;
+    if (!KF || tid == ftid) arow = __ldg(p.a + row);
+    if constexpr (KF) {
+      if (tid == ftid) u_old = __ldcg(p.U + row);
+    }
     T* grow = plan + int64_t(row) * ldp;
-    float u_old = 1.0f;
-    if constexpr (KF) u_old = __ldcg(p.U + row);
 
     // Column step of iteration t-1 on this row, then its sum.  Kernel form:
     // the row sum of U_i K_ij V_j is U_i sum_j K_ij V_j; K stays in x.
@@ -320,23 +328,33 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
       }
     }
     float tot = 0.0f;
-    for (uint32_t r = 0; r < cs; ++r)
+    if (!KF || tid == ftid) {
+      for (uint32_t r = 0; r < cs; ++r)
 #pragma unroll
-      for (int w = 0; w < NW; ++w) tot += rb[r * NW + w];
+        for (int w = 0; w < NW; ++w) tot += rb[r * NW + w];
+    }
 
     // Row step of iteration t.
     if constexpr (KF) {
-      // Kernel form: U_i <- U_i alpha_i 2^e_t; column partials of U_i K_ij
-      // (the column sums are V_j 2^-e_t times these).
-      tot *= u_old;
-      const float u_new = u_old * rescale_factor(arow, tot, p.fi, st) * gauge;
-      if (cr == 0 && tid == 0) {
-        p.U[row] = u_new;
-        if (p.save_r) {  // history for the adjoint: r_t and U_t of this row
-          p.save_r[row] = tot;
-          p.save_U[row] = u_new;
+      // Kernel form: U_i <- U_i alpha_i 2^e_t, formed once per row (one power
+      // per row rather than one per thread) and handed over through shared
+      // memory; column partials of U_i K_ij (the column sums are V_j 2^-e_t
+      // times these).
+      float* ufq = uf + (q & 1);
+      if (tid == ftid) {
+        tot *= u_old;
+        const float u_new = u_old * rescale_factor(arow, tot, p.fi, st) * gauge;
+        *ufq = u_new;
+        if (cr == 0) {
+          p.U[row] = u_new;
+          if (p.save_r) {  // history for the adjoint: r_t and U_t of this row
+            p.save_r[row] = tot;
+            p.save_U[row] = u_new;
+          }
         }
       }
+      __syncthreads();
+      const float u_new = *ufq;
 #pragma unroll
       for (int k = 0; k < KV; ++k)
 #pragma unroll
@@ -361,7 +379,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
         }
       }
     }
-    if (p.track && cr == 0 && tid == 0) {
+    if (p.track && cr == 0 && tid == ftid) {
       auto kahan = [](float& sum, float& comp, float v) {
         const float y = v - comp;
         const float t2 = sum + y;
@@ -391,7 +409,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
       }
     }
   }
-  if (p.track && cr == 0 && tid == 0 && done_rows > 0) {
+  if (p.track && cr == 0 && tid == ftid && done_rows > 0) {
     atomicAdd(&p.err_next[0], double(err_num) - double(err_num_c));
     atomicAdd(&p.err_next[1], double(err_den) - double(err_den_c));
   }
