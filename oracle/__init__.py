@@ -9,9 +9,11 @@ The oracle shares no code, header, table or helper with the CUDA library in
 Modules
 -------
 ``uot``      the literal Sinkhorn-UOT rule of Section 2.1 in FP64 (plain numpy),
-             the transport cost, the FP64 adjoint of the unrolled iterations.
-``convex``   brute-force entropic-OT solve through the smooth dual (scipy), used
-             only to pin the oracle's fixed point on tiny problems.
+             the scaling-vector (POT) form of the unbalanced iteration, the
+             transport cost, the FP64 adjoint of the unrolled iterations.
+``convex``   brute-force entropic-OT solves (balanced: Newton on the smooth
+             dual; unbalanced: Newton on the plan entries), used only to pin
+             the oracle's fixed points on tiny problems.
 ``sharded``  the row-partitioned form of Algorithm 1 with an explicit
              all-reduce of the column sums (Section 5.5), used by the gloo tests.
 """
@@ -26,6 +28,7 @@ from .uot import (  # noqa: F401
     row_step,
     col_step,
     sinkhorn,
+    sinkhorn_pot,
     transport_cost,
     sinkhorn_grad,
     kernel_form_scalings,

@@ -1,4 +1,4 @@
-"""Brute-force solve of the balanced entropic OT problem on tiny inputs.
+"""Brute-force solves of the entropic OT problems on tiny inputs.
 
 TEST INFRASTRUCTURE ONLY.  This module is not a Sinkhorn iteration: it maximises
 the smooth dual of
@@ -76,3 +76,62 @@ def entropic_ot_newton(C, p, q, reg: float, tol: float = 1e-14, max_iter: int = 
         phi = phi + s * d_phi
         psi = psi + s * d_psi
     return plan(phi, psi)
+
+
+def uot_objective(P, C, a, b, reg: float, reg_m: float) -> float:
+    """``<P,C> + reg sum P (log P - 1) + reg_m KL(P1|a) + reg_m KL(P^T 1|b)`` with
+    the generalised ``KL(x|y) = sum x log(x/y) - x + y`` (``reg_m = inf``:
+    the marginal terms become constraints and are left out)."""
+    P = np.asarray(P, np.float64)
+    r, c = P.sum(axis=1), P.sum(axis=0)
+
+    def kl(x, y):
+        return float(np.sum(x * np.log(x / y) - x + y))
+
+    val = float(np.sum(P * C) + reg * np.sum(P * (np.log(P) - 1.0)))
+    if np.isfinite(reg_m):
+        val += reg_m * (kl(r, a) + kl(c, b))
+    return val
+
+
+def uot_newton(C, a, b, reg: float, reg_m: float, tol: float = 1e-13, max_iter: int = 200):
+    """Minimiser of ``uot_objective`` over positive plans by Newton's method in
+    the plan entries themselves (N*M unknowns; tiny problems only).
+
+    Gradient ``C_ij + reg log P_ij + reg_m log(r_i/a_i) + reg_m log(c_j/b_j)``;
+    Hessian ``reg/P_ij`` on the diagonal plus ``reg_m/r_i`` between entries of
+    row i and ``reg_m/c_j`` between entries of column j (positive definite).
+    Steps are cut to keep every entry positive and to decrease the objective.
+    """
+    C = np.asarray(C, np.float64)
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if not np.isfinite(reg_m):
+        raise ValueError("reg_m must be finite (the balanced case is entropic_ot_newton)")
+    N, M = C.shape
+    P = np.full((N, M), np.sqrt(a.sum() * b.sum()) / (N * M))
+    rows = np.repeat(np.arange(N), M)
+    cols = np.tile(np.arange(M), N)
+    same_row = (rows[:, None] == rows[None, :]).astype(np.float64)
+    same_col = (cols[:, None] == cols[None, :]).astype(np.float64)
+    for _ in range(max_iter):
+        r, c = P.sum(axis=1), P.sum(axis=0)
+        g = (C + reg * np.log(P) + reg_m * np.log(r / a)[:, None]
+             + reg_m * np.log(c / b)[None, :]).ravel()
+        if np.max(np.abs(g)) <= tol:
+            break
+        p = P.ravel()
+        H = np.diag(reg / p) + reg_m * same_row / r[rows][:, None] + reg_m * same_col / c[cols][:, None]
+        step = np.linalg.solve(H, -g)
+        # Stay inside the positive orthant, then backtrack on the objective.
+        neg = step < 0
+        smax = min(1.0, 0.99 * float(np.min(-p[neg] / step[neg]))) if neg.any() else 1.0
+        base = uot_objective(P, C, a, b, reg, reg_m)
+        s = smax
+        while s > 1e-14:
+            Pn = (p + s * step).reshape(N, M)
+            if uot_objective(Pn, C, a, b, reg, reg_m) <= base + 1e-15 * abs(base):
+                break
+            s *= 0.5
+        P = (p + s * step).reshape(N, M)
+    return P

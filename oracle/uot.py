@@ -26,7 +26,9 @@ notes of the repository):
   ``t % check_every == 0``.
 
 Parity status: no function here can be pinned to numbers printed in the paper
-(it prints none).  ``sinkhorn`` is pinned by closed forms (1x1, rank-one cost),
+(it prints none).  ``sinkhorn_pot`` is pinned by the brute-force minimiser of the
+unbalanced objective, by the 1x1 closed form and by ``sinkhorn`` at ``fi = 1``.
+``sinkhorn`` is pinned by closed forms (1x1, rank-one cost),
 the textbook balanced Sinkhorn at ``fi = 1``, the closed-form fixed point
 checked by a brute-force convex solve, per-step identities and symmetries;
 ``sinkhorn_grad`` by FP64 central differences and by torch autograd of the
@@ -159,6 +161,53 @@ def sinkhorn(P0, a, b, reg: float, reg_m: float, iters: int, tol: float = 0.0,
         r_prev = r
         if tol > 0 and t >= 2 and t % check_every == 0 and res.err <= tol:
             break
+    return res
+
+
+def sinkhorn_pot(K, a, b, reg: float, reg_m: float, iters: int, tol: float = 0.0,
+                 check_every: int = 1) -> OracleResult:
+    """The scaling-vector form of the unbalanced iteration (the update of POT's
+    ``sinkhorn_unbalanced``), row step first:
+
+        u <- (a / (K v))^fi,    then    v <- (b / (K^T u))^fi,
+
+    with the plan ``diag(u) K diag(v)`` and ``u = v = 1`` at the start, ``K``
+    the initial plan.  It is NOT the rule Section 2.1 prints: written as a
+    rescale of the plan, its row factor is the printed ``(a_i/rowsum_i)^fi``
+    times ``u_i^(fi-1)``, so the two agree only when ``fi = 1``.  Its fixed
+    point minimises ``<P,C> + reg sum P (log P - 1) + reg_m KL(P1|a) +
+    reg_m KL(P^T 1|b)`` (see ``convex.uot_newton``).  The degenerate readings of
+    ``scaling_factor`` apply to the ratios ``a/(Kv)`` and ``b/(K^T u)``; the
+    stopping error is the one of ``sinkhorn`` (row sums of the plan before each
+    row step).
+    """
+    if iters < 0:
+        raise ValueError("iters must be >= 0")
+    if check_every < 1:
+        raise ValueError("check_every must be >= 1")
+    fi = fi_exponent(reg, reg_m)
+    K = np.asarray(K, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    u = np.ones(K.shape[0])
+    v = np.ones(K.shape[1])
+    res = OracleResult(plan=K.copy(), iters_done=0, err=math.inf, status=0)
+    r_prev = None
+    for t in range(1, iters + 1):
+        Kv = K @ v
+        r = u * Kv
+        u, s1 = scaling_factor(a, Kv, fi)
+        Ktu = K.T @ u
+        v, s2 = scaling_factor(b, Ktu, fi)
+        res.status |= s1 | s2
+        res.iters_done = t
+        if r_prev is not None:
+            den = r.sum()
+            res.err = float(np.abs(r - r_prev).sum() / den) if den > 0 else math.inf
+        r_prev = r
+        if tol > 0 and t >= 2 and t % check_every == 0 and res.err <= tol:
+            break
+    res.plan = u[:, None] * K * v[None, :]
     return res
 
 

@@ -269,3 +269,70 @@ def test_grad_matches_torch_autograd(N, M, T):
     np.testing.assert_allclose(dC, Ct.grad.numpy(), rtol=1e-8, atol=1e-12 * np.abs(dC).max())
     np.testing.assert_allclose(da, at.grad.numpy(), rtol=1e-8, atol=1e-12 * np.abs(da).max())
     np.testing.assert_allclose(db, bt.grad.numpy(), rtol=1e-8, atol=1e-12 * np.abs(db).max())
+
+
+# --- the scaling-vector (POT) form of the unbalanced iteration -------------
+
+
+@pytest.mark.parametrize("reg,reg_m", [(0.5, 1.0), (0.3, 0.4), (1.0, 5.0)])
+def test_pot_rule_fixed_point_minimises_uot_objective(reg, reg_m):
+    """The limit of u <- (a/Kv)^fi, v <- (b/K^T u)^fi is the minimiser of
+    <P,C> + reg sum P(log P - 1) + reg_m KL(P1|a) + reg_m KL(P^T1|b), found
+    here independently by Newton's method on the plan entries."""
+    C, a, b = rand_problem(11, 7, 5, mass_a=1.0, mass_b=1.7)
+    res = oracle.sinkhorn_pot(oracle.init_plan(C, reg), a, b, reg, reg_m, 4000)
+    ref = convex.uot_newton(C, a, b, reg, reg_m)
+    np.testing.assert_allclose(res.plan, ref, rtol=1e-9)
+    f_ref = convex.uot_objective(ref, C, a, b, reg, reg_m)
+    rng = np.random.default_rng(0)
+    for _ in range(5):  # a local minimum: nearby plans cost more
+        Pn = ref * np.exp(1e-3 * rng.standard_normal(ref.shape))
+        assert convex.uot_objective(Pn, C, a, b, reg, reg_m) > f_ref
+
+
+@pytest.mark.parametrize("reg,reg_m", [(0.05, 1.0), (0.3, 0.5), (1.0, 0.2)])
+def test_pot_rule_one_by_one_closed_form(reg, reg_m):
+    """1x1 with K = k: x = log u, y = log v obey x_t = fi (A - y_{t-1}),
+    y_t = fi (B - x_t) with A = log(a/k), B = log(b/k), y_0 = 0, so
+    y_T = d (1 - q^T)/(1 - q) with q = fi^2, d = fi B - fi^2 A."""
+    fi = oracle.fi_exponent(reg, reg_m)
+    a, b, k = 0.37, 2.9, 0.011
+    A, B = math.log(a / k), math.log(b / k)
+    q, d = fi * fi, fi * B - fi * fi * A
+    for T in range(1, 41):
+        y_prev = d * (1 - q ** (T - 1)) / (1 - q)
+        x = fi * (A - y_prev)
+        y = fi * (B - x)
+        res = oracle.sinkhorn_pot([[k]], [a], [b], reg, reg_m, T)
+        assert res.plan[0, 0] == pytest.approx(k * math.exp(x + y), rel=1e-12)
+
+
+def test_pot_rule_balanced_case_equals_the_printed_rule():
+    """fi = 1: both rules are balanced Sinkhorn, iterate by iterate."""
+    C, a, b = rand_problem(5, 6, 9, mass_a=1.3, mass_b=1.3)
+    P0 = oracle.init_plan(C, 0.2)
+    for T in (1, 2, 7, 30):
+        lit = oracle.sinkhorn(P0, a, b, 0.2, math.inf, T)
+        pot = oracle.sinkhorn_pot(P0, a, b, 0.2, math.inf, T)
+        np.testing.assert_allclose(pot.plan, lit.plan, rtol=1e-12)
+
+
+def test_pot_rule_differs_from_the_printed_rule():
+    """fi < 1: the printed rule and the scaling-vector rule have different
+    limits (the printed rule's is balanced between rescaled marginals)."""
+    C, a, b = rand_problem(9, 7, 5, mass_a=1.0, mass_b=1.5)
+    P0 = oracle.init_plan(C, 0.3)
+    lit = oracle.sinkhorn(P0, a, b, 0.3, 0.5, 3000).plan
+    pot = oracle.sinkhorn_pot(P0, a, b, 0.3, 0.5, 3000).plan
+    assert np.max(np.abs(lit - pot) / pot) > 0.05
+    # The printed rule's limit has equal row and column mass; the
+    # scaling-vector rule's generally does not.
+    assert lit.sum(axis=1).sum() == pytest.approx(lit.sum(axis=0).sum(), rel=1e-12)
+
+
+def test_pot_rule_zero_target_and_stopping():
+    C, a, b = rand_problem(2, 5, 4)
+    a[2] = 0.0
+    res = oracle.sinkhorn_pot(oracle.init_plan(C, 0.3), a, b, 0.3, 1.0, 200, tol=1e-9)
+    assert np.all(res.plan[2] == 0.0) and res.status == 0
+    assert res.iters_done < 200 and res.err <= 1e-9
