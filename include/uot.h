@@ -59,6 +59,21 @@ typedef enum uot_dtype { UOT_F32 = 0, UOT_BF16 = 1, UOT_F16 = 2 } uot_dtype;
  *            plain GPU reference the fused path is compared against. */
 typedef enum uot_algo { UOT_ALGO_FUSED = 0, UOT_ALGO_MULTIPASS = 1 } uot_algo;
 
+/* Which update the iteration applies.
+ * PAPER: the rule of Section 2.1 as printed: each row of the plan is
+ *        rescaled by (a_i / rowsum_i)^fi, then each column by
+ *        (b_j / colsum_j)^fi.  Its limit is a balanced entropic OT plan
+ *        between rescaled marginals (the masses meet in between).
+ * POT:   the scaling-vector form of unbalanced Sinkhorn (the update of POT's
+ *        sinkhorn_unbalanced): with the plan diag(u) K diag(v),
+ *        u <- (a / (K v))^fi, then v <- (b / (K^T u))^fi.  As a plan rescale
+ *        this is the PAPER factor times u_i^(fi - 1).  Its limit minimises
+ *        <P,C> + reg sum P (log P - 1) + reg_m KL(P 1 | a) + reg_m KL(P^T 1 | b).
+ *        Only the kernel form keeps u and v, so only the kernel-form entry
+ *        points and the batched engines accept it; the two rules agree when
+ *        fi = 1.  The adjoint (uot_sinkhorn_backward) is for PAPER only. */
+typedef enum uot_rule { UOT_RULE_PAPER = 0, UOT_RULE_POT = 1 } uot_rule;
+
 /* Bits of uot_result.dev_status. */
 #define UOT_DEV_ZERO_SUM 1u
 #define UOT_DEV_NONFINITE 2u
@@ -74,7 +89,8 @@ typedef struct uot_options {
   int32_t max_ctas;     /* 0 = as many CTAs as fit; else at most this many per
                            launch (to run several solves side by side, e.g.
                            as parallel branches of one CUDA graph)          */
-  int32_t reserved[2];  /* must be 0                                          */
+  int32_t rule;         /* uot_rule (default UOT_RULE_PAPER)                  */
+  int32_t reserved[1];  /* must be 0                                          */
   void* pass_events[2]; /* optional cudaEvent_t pair: uot_sinkhorn records
                            [0] on `stream` just before its first iteration
                            pass and [1] just after its last (NULL = none);
@@ -317,7 +333,7 @@ typedef struct uot_problem {
   const float* b;    /* device, length m */
   float reg, reg_m;  /* fi = reg_m / (reg_m + reg); reg_m = +INFINITY gives fi = 1 */
   int32_t iters;     /* iterations for this problem (>= 0) */
-  int32_t reserved;  /* must be 0 */
+  int32_t rule;      /* uot_rule of this problem */
 } uot_problem;
 
 /* Schedule knobs (uot_batch_default_tuning fills the defaults):

@@ -42,6 +42,7 @@ class Batch:
             d.a = a.data_ptr()
             d.b = b.data_ptr()
             d.reg, d.reg_m, d.iters = p.reg, p.reg_m, p.iters
+            d.rule = getattr(p, "rule", uot.UOT_RULE_PAPER)
             self.descs.append(d)
         self.ws = uot.workspace_bytes(uot.uot_batched_workspace_size(self.descs), self.device)
         self.tuning = None

@@ -32,7 +32,7 @@ static uot_options resolve(const uot_options* opt) {
 }
 
 static bool reserved_zero(const uot_options& o) {
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < 1; ++k)
     if (o.reserved[k] != 0) return false;
   return true;
 }
@@ -129,6 +129,11 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
   if (!(reg > 0.0f) || !std::isfinite(reg) || !(reg_m > 0.0f) || iters < 0)
     return UOT_ERR_INVALID_ARG;
   if (std::isnan(tol) || std::isinf(tol) || !reserved_zero(o)) return UOT_ERR_INVALID_ARG;
+  if (o.rule != UOT_RULE_PAPER && o.rule != UOT_RULE_POT) return UOT_ERR_INVALID_ARG;
+  // The scaling-vector rule needs the scalings (kernel form); the adjoint's
+  // history is for the rule of Section 2.1.
+  if (o.rule == UOT_RULE_POT && (!kf || hist)) return UOT_ERR_UNSUPPORTED;
+  const bool pot = o.rule == UOT_RULE_POT;
   if (o.algo != UOT_ALGO_FUSED && o.algo != UOT_ALGO_MULTIPASS) return UOT_ERR_INVALID_ARG;
   if (o.cluster < 0 || o.cluster > 8 || o.tile < 0 || o.max_ctas < 0) return UOT_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(mat) % esize(o.dtype) ||
@@ -172,7 +177,7 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
   if (launch_reset(ws, L, b, M, s) != cudaSuccess) return UOT_ERR_CUDA;
   if (kf && launch_kform_reset(U, N, std::ldexp(1.0f, -int(std::lround(k_log2_scale))),
                                reinterpret_cast<float*>(ws + L.beta), M, int(L.mpad), a, b, fi,
-                               reinterpret_cast<double*>(ws + L.log2k), s) != cudaSuccess)
+                               pot, reinterpret_cast<double*>(ws + L.log2k), s) != cudaSuccess)
     return UOT_ERR_CUDA;
   uint8_t* hb = static_cast<uint8_t*>(hist);
   if (hist && launch_hist_init(hb, N, M, iters, std::ldexp(1.0f, -int(std::lround(k_log2_scale))),
@@ -215,6 +220,8 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
     A.log2k = reinterpret_cast<const double*>(ws + L.log2k);
     A.beta = reinterpret_cast<const float*>(ws + L.beta);
     A.beta_out = reinterpret_cast<float*>(ws + L.beta);
+    A.pot = pot ? 1 : 0;
+    A.kscale = std::ldexp(1.0f, int(std::lround(k_log2_scale)));
     int* ctr = reinterpret_cast<int*>(ws + L.ctr);
     float* c[3];
     double* er[3];

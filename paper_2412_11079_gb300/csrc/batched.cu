@@ -241,7 +241,8 @@ __device__ void sweep(const BatchProblem& P, bool finish, const float (&V)[BKV][
         } else {
           float sum = 0.0f;
           for (int w = 0; w < wpg; ++w) sum += rp[r * wpg + w];
-          const float u_new = u_old * rescale_factor(As[i], u_old * sum, fi, st) * gauge;
+          const float u_new = P.pot ? rescale_factor(As[i], sum, fi, st)
+                                    : u_old * rescale_factor(As[i], u_old * sum, fi, st) * gauge;
           Us[i] = u_new;
           uf[r] = u_new;
         }
@@ -445,7 +446,8 @@ __global__ void __launch_bounds__(BT, 2) batched_kernel(const BatchSched S) {
               if (j < m) {
                 const float v = Vsm[j];
                 const float cj = v * cv[u] * inv_gauge;
-                Vsm[j] = v * rescale_factor(bv[u], cj, P.fi, st) * inv_gauge;
+                Vsm[j] = P.pot ? rescale_factor(bv[u], cv[u], P.fi, st)
+                               : v * rescale_factor(bv[u], cj, P.fi, st) * inv_gauge;
               }
             }
           }
@@ -515,7 +517,7 @@ __global__ void batched_reset_kernel(const BatchProblem* probs, int nprob, int* 
       }
       const double f = double(P.fi);
       const double Lk = (f / (2.0 - f)) * log2(ta / tb);
-      *P.log2k = (ta > 0.0 && tb > 0.0 && isfinite(Lk)) ? Lk : 0.0;
+      *P.log2k = (!P.pot && ta > 0.0 && tb > 0.0 && isfinite(Lk)) ? Lk : 0.0;
     }
     if (threadIdx.x == 0) {
       P.ctl->status = 0;
@@ -618,6 +620,7 @@ uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uo
   for (int i = 0; i < nprob; ++i) {
     const uot_problem& q = probs[i];
     if (!q.plan || !q.a || !q.b || q.m > BW || q.n > INT32_MAX || q.ldp < q.m || q.iters < 0 ||
+        (q.rule != UOT_RULE_PAPER && q.rule != UOT_RULE_POT) ||
         !(q.reg > 0.0f) || !std::isfinite(q.reg) || !(q.reg_m > 0.0f) ||
         reinterpret_cast<uintptr_t>(q.plan) % 16 || (q.ldp % 4) != 0 ||
         reinterpret_cast<uintptr_t>(q.a) % 4 || reinterpret_cast<uintptr_t>(q.b) % 4)
@@ -731,6 +734,7 @@ uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uo
                                           : double(q.reg_m) / (double(q.reg_m) + double(q.reg));
     d.fi = float(fi);
     d.iters = q.iters;
+    d.pot = q.rule == UOT_RULE_POT ? 1 : 0;
     d.mpad = int((q.m + 63) & ~int64_t(63));
     d.ctl = reinterpret_cast<Control*>(ws + ctl_off) + i;
     d.c = reinterpret_cast<float*>(ws + off);

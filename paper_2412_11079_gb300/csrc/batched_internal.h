@@ -23,8 +23,9 @@ struct BatchProblem {
   float* c;       // 3 x mpad column sums of U K (ring)
   int* ctr;       // 3 row counters (ring)
   float* U;       // n row scalings
-  double* log2k;  // log2 of the fixed-point row factor (gauge)
+  double* log2k;  // log2 of the fixed-point row factor (gauge; 0 for the POT rule)
   Control* ctl;
+  int pot;        // scaling-vector rule: u <- (a / K v)^fi, v <- (b / K^T u)^fi
 };
 
 // Resident solver: a problem whose initial plan fits in the shared memory of

@@ -342,8 +342,12 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
       // times these).
       float* ufq = uf + (q & 1);
       if (tid == ftid) {
-        tot *= u_old;
-        const float u_new = u_old * rescale_factor(arow, tot, p.fi, st) * gauge;
+        const float s_kv = tot;  // sum_j K_ij V_j (K as stored)
+        tot *= u_old;            // r_i, the row sum of the plan
+        // Scaling-vector rule: u_i <- (a_i / (K v)_i)^fi with K = stored K / kscale
+        // and U = u / kscale; no gauge.
+        const float u_new = p.pot ? rescale_factor(arow * p.kscale, s_kv, p.fi, st) / p.kscale
+                                  : u_old * rescale_factor(arow, tot, p.fi, st) * gauge;
         *ufq = u_new;
         if (cr == 0) {
           p.U[row] = u_new;
@@ -426,10 +430,13 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
       const int j0 = sl * per, j1 = min(m, j0 + per);
       for (int j = j0 + tid; j < j1; j += THREADS) {
         if constexpr (KF) {
-          // V_j <- V_j (b_j / c_j)^fi 2^-e_t with c_j = V_j 2^-e_t sum_i U_i K_ij.
+          // V_j <- V_j (b_j / c_j)^fi 2^-e_t with c_j = V_j 2^-e_t sum_i U_i K_ij;
+          // scaling-vector rule: v_j <- (b_j / sum_i U_i K_ij)^fi.
           const float v = __ldcg(p.beta_out + j);
-          const float c = v * __ldcg(p.c_next + j) * inv_gauge;
-          const float v_new = v * rescale_factor(__ldg(p.b_ws + j), c, p.fi, st2) * inv_gauge;
+          const float d = __ldcg(p.c_next + j);
+          const float c = v * d * inv_gauge;
+          const float v_new = p.pot ? rescale_factor(__ldg(p.b_ws + j), d, p.fi, st2)
+                                    : v * rescale_factor(__ldg(p.b_ws + j), c, p.fi, st2) * inv_gauge;
           p.beta_out[j] = v_new;
           if (p.save_c) {  // history for the adjoint: c_t and V_t of this column
             p.save_c[j] = c;

@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(RT, 1) resident_kernel(const ResidentArgs A) {
         float sum = 0.0f;
         for (int w = 0; w < wpg; ++w) sum += rsp[w * nb + i];
         const float u_old = Ul[i];
-        Ul[i] = u_old * rescale_factor(al[i], u_old * sum, fi, st) * gauge;
+        Ul[i] = P.pot ? rescale_factor(al[i], sum, fi, st)
+                      : u_old * rescale_factor(al[i], u_old * sum, fi, st) * gauge;
       }
       __syncthreads();
       // (c) Column partials of U_i K_ij over this CTA's rows.
@@ -295,7 +296,8 @@ __global__ void __launch_bounds__(RT, 1) resident_kernel(const ResidentArgs A) {
           const int j = ch * 4 + e;
           if (j < m) {
             const float cj = vv[e] * cc[e] * inv_gauge;
-            vn[e] = vv[e] * rescale_factor(bs[j - ch0 * 4], cj, fi, st) * inv_gauge;
+            vn[e] = P.pot ? rescale_factor(bs[j - ch0 * 4], cc[e], fi, st)
+                          : vv[e] * rescale_factor(bs[j - ch0 * 4], cj, fi, st) * inv_gauge;
           } else {
             vn[e] = 0.0f;
           }

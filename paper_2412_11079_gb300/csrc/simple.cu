@@ -155,7 +155,8 @@ __global__ void kform_reset_kernel(float* U, int n, float u0, float* V_ws, int m
 // Kernel form: log2 k, k = (m_a / m_b)^(fi / (2 - fi)) the row factor at the
 // fixed point of the row-then-column rule (0 when a mass is 0 or not finite).
 __global__ void __launch_bounds__(1024) kform_gauge_kernel(const float* a, int n, const float* b,
-                                                           int m, float fi, double* log2k) {
+                                                           int m, float fi, bool pot,
+                                                           double* log2k) {
   __shared__ double part[2][32];
   double sa = 0.0, sb = 0.0;
   for (int i = threadIdx.x; i < n; i += 1024) sa += a[i];
@@ -175,7 +176,8 @@ __global__ void __launch_bounds__(1024) kform_gauge_kernel(const float* a, int n
     }
     const double f = double(fi);
     const double L = (f / (2.0 - f)) * log2(ta / tb);
-    *log2k = (ta > 0.0 && tb > 0.0 && isfinite(L)) ? L : 0.0;
+    // The scaling-vector rule converges in (U, V) itself: no drift, no gauge.
+    *log2k = (!pot && ta > 0.0 && tb > 0.0 && isfinite(L)) ? L : 0.0;
   }
 }
 
@@ -332,13 +334,13 @@ cudaError_t launch_init(const float* C, int64_t ldc, void* P, int64_t ldp, int n
 }
 
 cudaError_t launch_kform_reset(float* U, int n, float u0, float* V_ws, int m, int mpad,
-                               const float* a, const float* b, float fi, double* log2k,
+                               const float* a, const float* b, float fi, bool pot, double* log2k,
                                cudaStream_t s) {
   const int blocks = (max(n, mpad) + TB - 1) / TB;
   kform_reset_kernel<<<blocks, TB, 0, s>>>(U, n, u0, V_ws, m, mpad);
   cudaError_t e = last();
   if (e != cudaSuccess) return e;
-  kform_gauge_kernel<<<1, 1024, 0, s>>>(a, n, b, m, fi, log2k);
+  kform_gauge_kernel<<<1, 1024, 0, s>>>(a, n, b, m, fi, pot, log2k);
   return last();
 }
 

@@ -103,6 +103,8 @@ struct FusedArgs {
   float* save_U;       // U_t (n)
   float* save_c;       // c_t (m)
   float* save_V;       // V_t (m)
+  int pot;             // kernel form: scaling-vector rule (uot_rule POT)
+  float kscale;        // kernel form: storage scale of K (2^s; FP16 K is stored x 2^15)
 };
 
 // History of a kernel-form solve kept for the adjoint: a header, then for
@@ -154,7 +156,7 @@ cudaError_t fused_launch(bool kf, int k, int cs, int grid, size_t smem, bool tma
 cudaError_t launch_init(const float* C, int64_t ldc, void* P, int64_t ldp, int n, int m,
                         float reg, int dtype, float scale, cudaStream_t s);
 cudaError_t launch_kform_reset(float* U, int n, float u0, float* V_ws, int m, int mpad,
-                               const float* a, const float* b, float fi, double* log2k,
+                               const float* a, const float* b, float fi, bool pot, double* log2k,
                                cudaStream_t s);
 cudaError_t launch_kform_finish(float* V, int m, int iters, const uint8_t* ws, WsLayout L,
                                 double tol, cudaStream_t s);

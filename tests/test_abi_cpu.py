@@ -39,7 +39,8 @@ def test_status_strings_and_defaults(lib):
     assert "workspace" in uot.uot_status_string(uot.UOT_ERR_WORKSPACE)
     o = uot.UotOptions()
     lib.uot_default_options(ctypes.byref(o))
-    assert (o.dtype, o.algo, o.check_every, o.tile, o.cluster, o.max_ctas) == (0, 0, 1, 0, 0, 0)
+    assert (o.dtype, o.algo, o.check_every, o.tile, o.cluster, o.max_ctas, o.rule) == \
+        (0, 0, 1, 0, 0, 0, uot.UOT_RULE_PAPER)
 
 
 def test_workspace_size(lib):
@@ -94,9 +95,15 @@ def test_argument_validation_needs_no_gpu(lib):
         assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 1 << 20, ctypes.byref(bad), None,
                  None) == uot.UOT_ERR_INVALID_ARG
     bad = uot.options()
-    bad.reserved[1] = 1
+    bad.reserved[0] = 1
     assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 1 << 20, ctypes.byref(bad), None,
              None) == uot.UOT_ERR_INVALID_ARG
+    # unknown rule; the scaling-vector rule needs the kernel form
+    assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 1 << 20, ctypes.byref(uot.options(rule=2)),
+             None, None) == uot.UOT_ERR_INVALID_ARG
+    assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 1 << 20,
+             ctypes.byref(uot.options(rule=uot.UOT_RULE_POT)), None,
+             None) == uot.UOT_ERR_UNSUPPORTED
     g = lib.uot_init_kernel
     assert g(None, 4, P, 4, 4, 4, 0.1, None, None) == uot.UOT_ERR_INVALID_ARG
     assert g(P, 4, P, 4, 4, 4, -1.0, None, None) == uot.UOT_ERR_INVALID_ARG

@@ -79,6 +79,28 @@ def test_padded_rows_streaming_and_on_chip(uot):
     check_batch(uot, mixed_problems(), pad=8)
 
 
+@pytest.mark.parametrize("max_cluster", [0, 16])
+def test_pot_rule_in_both_engines(uot, max_cluster):
+    """Problems of a batch may use either rule; each matches its oracle, on
+    chip and streaming."""
+    from paper_2412_11079_gb300.batch import Batch
+    problems = mixed_problems() + on_chip_problems()[:6]
+    for k, p in enumerate(problems):
+        p.rule = uot.UOT_RULE_POT if k % 2 == 0 else uot.UOT_RULE_PAPER
+    B = Batch(problems)
+    B.init_plans()
+    B.prepare(uot.batch_tuning(resident_max_cluster=max_cluster))
+    B.run()
+    res = B.results()
+    for p, plan, r in zip(problems, B.plans, res):
+        P0 = oracle.init_plan(p.C, p.reg)
+        ref = (oracle.sinkhorn_pot(P0, p.a, p.b, p.reg, p.reg_m, p.iters)
+               if p.rule == uot.UOT_RULE_POT else
+               oracle.sinkhorn(P0, p.a, p.b, p.reg, p.reg_m, p.iters))
+        assert r.iters_done == p.iters and r.dev_status == 0
+        assert rel_err(plan.double().cpu().numpy(), ref.plan) <= FP32_TOL, (p.name, p.rule)
+
+
 def test_large_teams_on_small_problems(uot):
     """Tiny target work per CTA forces multi-CTA teams (software barriers,
     shared row counters) even for small problems."""

@@ -42,12 +42,12 @@ def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def kform_gpu(uot, p, dtype=torch.float32, log2_scale=0, iters=None, tol=0.0, ld=None):
+def kform_gpu(uot, p, dtype=torch.float32, log2_scale=0, iters=None, tol=0.0, ld=None, rule=0):
     n, m = p.C.shape
     C = dev(p.C)
     store = torch.zeros((n, ld or m), dtype=dtype, device="cuda")
     K = store[:, :m]
-    opt = uot.options(uot.dtype_code(dtype))
+    opt = uot.options(uot.dtype_code(dtype), rule=rule)
     uot.uot_init_kernel_scaled(C, K, p.reg, log2_scale, opt)
     U, V, res = uot.uot_sinkhorn_kform(K, dev(p.a), dev(p.b), p.reg, p.reg_m,
                                        p.iters if iters is None else iters, tol, log2_scale,
@@ -147,3 +147,65 @@ def test_kernel_form_rejects_bad_arguments(uot):
     with pytest.raises(uot.UotError):
         uot.uot_sinkhorn_kform(K, dev(p.a), dev(p.b), p.reg, p.reg_m, 2,
                                opt=uot.options(algo=uot.UOT_ALGO_MULTIPASS))
+
+
+# --- the scaling-vector (POT) rule -------------------------------------------
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (3, 5), (33, 31), (127, 1000), (1000, 1025),
+                                 (65, 16387), (40, 40000)])
+def test_pot_rule_fp32_kernel_form_matches_oracle(uot, n, m):
+    """u <- (a/Kv)^fi, v <- (b/K^T u)^fi on read-only K against the FP64
+    oracle of the same rule (FP32 tolerance), rows from 1 to 40000 wide
+    (clusters of CTAs per row above 16384)."""
+    p = workloads.uniform2d(seed=n * 17 + m, n=n, m=m, reg=0.1, reg_m=0.7, iters=25)
+    plan, cost, U, V, res = kform_gpu(uot, p, rule=uot.UOT_RULE_POT)
+    ref = oracle.sinkhorn_pot(oracle.init_plan(p.C, p.reg), p.a, p.b, p.reg, p.reg_m, p.iters)
+    assert res.iters_done == p.iters and res.dev_status == 0
+    assert rel_err(plan, ref.plan) <= FP32_TOL
+    c_ref = oracle.transport_cost(ref.plan, p.C)
+    assert abs(cost - c_ref) <= FP32_TOL * abs(c_ref)
+
+
+@pytest.mark.parametrize("dtype,log2_scale", [(torch.bfloat16, 0), (torch.float16, 15)])
+def test_pot_rule_reduced_precision_kernel_form(uot, dtype, log2_scale):
+    """16-bit K (FP16 stored x 2^15, the scale folded into U) under the
+    scaling-vector rule, on a 2048^2 instance of the reduced-precision
+    generator; 1e-2 on plan entries and cost."""
+    p = workloads.precision_case(seed=5, n=2048, m=2048, iters=100)
+    plan, cost, U, V, res = kform_gpu(uot, p, dtype=dtype, log2_scale=log2_scale,
+                                      rule=uot.UOT_RULE_POT)
+    ref = oracle.sinkhorn_pot(oracle.init_plan(p.C, p.reg), p.a, p.b, p.reg, p.reg_m, p.iters)
+    assert res.dev_status == 0
+    assert rel_err(plan, ref.plan) <= LOW_TOL
+    c_ref = oracle.transport_cost(ref.plan, p.C)
+    assert abs(cost - c_ref) <= LOW_TOL * abs(c_ref)
+
+
+def test_pot_rule_stopping_rule(uot):
+    """The device stopping rule under the scaling-vector rule stops where the
+    oracle of that rule stops."""
+    p = workloads.uniform2d(seed=3, n=300, m=200, reg=0.2, reg_m=2.0, iters=400)
+    tol = 1e-6
+    plan, cost, U, V, res = kform_gpu(uot, p, tol=tol, rule=uot.UOT_RULE_POT)
+    ref = oracle.sinkhorn_pot(oracle.init_plan(p.C, p.reg), p.a, p.b, p.reg, p.reg_m, p.iters,
+                              tol=tol)
+    assert ref.iters_done < p.iters
+    assert abs(res.iters_done - ref.iters_done) <= 1 and res.err <= tol
+    ref2 = oracle.sinkhorn_pot(oracle.init_plan(p.C, p.reg), p.a, p.b, p.reg, p.reg_m,
+                               res.iters_done)
+    assert rel_err(plan, ref2.plan) <= FP32_TOL
+
+
+def test_pot_rule_rejected_where_unsupported(uot):
+    """In-place plans keep no scalings, and the adjoint is for the printed
+    rule: both refuse the scaling-vector rule."""
+    p = workloads.uniform2d(seed=4, n=16, m=12, iters=3)
+    P = torch.from_numpy(oracle.init_plan(p.C, p.reg).astype(np.float32)).cuda()
+    with pytest.raises(uot.UotError, match="unsupported"):
+        uot.uot_sinkhorn(P, dev(p.a), dev(p.b), p.reg, p.reg_m, 3, 0.0,
+                         opt=uot.options(rule=uot.UOT_RULE_POT))
+    K = torch.from_numpy(oracle.init_plan(p.C, p.reg).astype(np.float32)).cuda()
+    with pytest.raises(uot.UotError, match="unsupported"):
+        uot.uot_sinkhorn_kform_save(K, dev(p.a), dev(p.b), p.reg, p.reg_m, 3,
+                                    opt=uot.options(rule=uot.UOT_RULE_POT))
