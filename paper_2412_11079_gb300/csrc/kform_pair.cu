@@ -1,0 +1,426 @@
+// Kernel-form pass over 16-bit K, two rows per step.
+//
+// The same iteration as fused_pass_kernel<T, ..., KF = true> (the plan kept
+// as diag(U) K diag(V), K read-only, FP32 scalings; one pass per iteration of
+// Section 2.1's rule, Algorithm 1's single sweep), for BF16/FP16 K when a row
+// fits one CTA and bulk copies apply.  A 16-bit row is half the bytes of an
+// FP32 row, so with one row per step the fixed latency of a step (barrier,
+// the row factor's power, the refill) bounds the pass well below HBM
+// bandwidth.  Here each step takes two consecutive rows: both row sums share
+// one barrier, two threads of the last warp form the two row factors, a
+// second barrier hands them to every thread, and the rows are read from
+// shared memory a second time for the column partials (holding two rows in
+// registers beside the column scalings and partial sums does not fit); the
+// slot is refilled after that second read.
+//
+// Rows are taken in pairs from the pass's counter (the next pair fetched one
+// step ahead), alternating direction between passes; the column factors of
+// the next pass are formed by the CTAs that finish last (finish_pass_job).
+// The stopping rule's row sums are accumulated by the two factor threads.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "fused_kernel.cuh"
+
+namespace uot {
+
+namespace {
+
+template <typename T, int THREADS, int KV>
+__global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs p) {
+  using E = Elem<T>;
+  constexpr int VE = E::VE;  // 8 elements per 16-byte vector
+  constexpr int NW = THREADS / 32;
+  constexpr int W = KV * VE * THREADS;
+  constexpr int ROW_BYTES = W * int(sizeof(T));
+  constexpr int SLOT_BYTES = 2 * ROW_BYTES;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int stages = p.stages;
+  unsigned char* ring = smem;
+  float* red = reinterpret_cast<float*>(smem + size_t(stages) * SLOT_BYTES);  // [2][2][NW]
+  float* uf = red + 4 * NW;                                                    // [2][2]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(uf + 4);
+  int* slot_rows = reinterpret_cast<int*>(bars + stages);  // [stages][2]
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  Control* ctl = p.ctl;
+  if (p.track) {
+    if (*reinterpret_cast<volatile int32_t*>(&ctl->done)) return;
+    if (p.check_prev) {
+      const double num = p.err_prev[0], den = p.err_prev[1];
+      if (den > 0.0 && num <= p.tol * den) {
+        if (blockIdx.x == 0 && tid == 0) {
+          ctl->stop_iter = p.t - 1;
+          ctl->err = num / den;
+          __threadfence();
+          ctl->done = 1;
+        }
+        return;
+      }
+    }
+  }
+
+  const int m = p.m, n = p.n;
+  float gauge = 1.0f, inv_gauge = 1.0f;
+  {
+    const int e = gauge_exponent(p.t, float(*p.log2k));
+    gauge = ldexpf(1.0f, e);
+    inv_gauge = ldexpf(1.0f, -e);
+  }
+  const int valid = min(W, m);
+  const uint32_t copy_bytes = uint32_t((size_t(valid) * sizeof(T)) & ~size_t(15));
+  const T* plan = reinterpret_cast<const T*>(p.plan);
+  const int64_t ldp = p.ldp;
+  uint32_t st = 0;
+  const uint64_t policy = policy_evict_first();
+  int issued = 0, next_base = n;
+
+  if (tid == 0) {
+    for (int s2 = 0; s2 < stages; ++s2) mbar_init(&bars[s2], 1);
+    fence_mbar_init();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  const bool flip = (p.t & 1) == 0;
+  // Arms the slot of step q with the rows base, base + 1 (those below n).
+  auto arm = [&](int q, int base) {
+    const int slot = q % stages;
+    if (base < n) {
+      int ra = base, rb = base + 1 < n ? base + 1 : -1;
+      if (flip) {
+        ra = n - 1 - ra;
+        if (rb >= 0) rb = n - 1 - rb;
+      }
+      slot_rows[2 * slot] = ra;
+      slot_rows[2 * slot + 1] = rb;
+      if (copy_bytes) {
+        mbar_arrive_expect_tx(&bars[slot], copy_bytes * (rb >= 0 ? 2u : 1u));
+        bulk_load(ring + size_t(slot) * SLOT_BYTES, plan + int64_t(ra) * ldp, copy_bytes,
+                  &bars[slot], policy);
+        if (rb >= 0)
+          bulk_load(ring + size_t(slot) * SLOT_BYTES + ROW_BYTES, plan + int64_t(rb) * ldp,
+                    copy_bytes, &bars[slot], policy);
+      } else {
+        mbar_arrive(&bars[slot]);
+      }
+    } else {
+      slot_rows[2 * slot] = -1;
+      mbar_arrive(&bars[slot]);
+    }
+  };
+  if (tid == 0) {
+    const int base = atomicAdd(p.row_ctr, 2 * stages);
+    for (int q = 0; q < stages; ++q) arm(q, base + 2 * q);
+    issued = stages;
+    if (base + 2 * stages < n) next_base = atomicAdd(p.row_ctr, 2);
+  }
+
+  // Column scalings V of this thread's columns (zero-padded buffer).
+  float V[KV][VE];
+#pragma unroll
+  for (int k = 0; k < KV; ++k) {
+    const int cc = (k * THREADS + tid) * VE;
+    if (cc < m) {
+#pragma unroll
+      for (int e = 0; e < VE; e += 4) {
+        const float4 b4 = __ldcg(reinterpret_cast<const float4*>(p.beta + cc + e));
+        V[k][e] = b4.x; V[k][e + 1] = b4.y; V[k][e + 2] = b4.z; V[k][e + 3] = b4.w;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < VE; ++e) V[k][e] = 0.0f;
+    }
+  }
+  {
+    const int g = blockIdx.x * THREADS + tid, gs = gridDim.x * THREADS;
+    for (int j = g; j < p.mpad; j += gs) p.c_clear[j] = 0.0f;
+    if (blockIdx.x == 0 && tid == 0) {
+      *p.ctr_clear = 0;
+      *p.arrive_clear = 0;
+      *p.slice_clear = 0;
+    }
+    if (p.track && blockIdx.x == 0 && tid < 2) p.err_clear[tid] = 0.0;
+  }
+
+  float cacc[KV][VE];
+#pragma unroll
+  for (int k = 0; k < KV; ++k)
+#pragma unroll
+    for (int e = 0; e < VE; ++e) cacc[k][e] = 0.0f;
+
+  // Two factor threads in the last warp: THREADS-1 for the first row of a
+  // step, THREADS-2 for the second.
+  const int fh = THREADS - 1 - tid;  // 0 or 1 for the factor threads
+  const bool factor_thread = fh == 0 || fh == 1;
+  float err_num = 0.0f, err_den = 0.0f, err_num_c = 0.0f, err_den_c = 0.0f;
+  bool broken = false;
+  int done_steps = 0;
+
+  // Packed row chunk k of a row (bulk-copied part from the slot, the rest
+  // from global memory, columns >= m as zeros).
+  auto load_chunk = [&](const unsigned char* srow, int row, int k, float (&f)[VE]) {
+    const int li = k * THREADS + tid;
+    const int cc = li * VE;
+    if ((cc + VE) * int(sizeof(T)) <= int(copy_bytes)) {
+      E::unpack(ld_shared_v4(srow + size_t(li) * 16), f);
+    } else {
+#pragma unroll
+      for (int e = 0; e < VE; ++e) f[e] = (cc + e < m) ? E::load1(plan + int64_t(row) * ldp + cc + e) : 0.0f;
+    }
+  };
+
+  for (int q = 0;; ++q) {
+    const int slot = q % stages;
+    if (!broken && !mbar_wait_bounded(&bars[slot], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS)) {
+      broken = true;
+      st |= DEV_TIMEOUT;
+    }
+    const int ra = *reinterpret_cast<volatile int*>(&slot_rows[2 * slot]);
+    if (ra < 0 || ra >= n) break;  // uniform: every thread reads the same slot
+    const int rb = *reinterpret_cast<volatile int*>(&slot_rows[2 * slot + 1]);
+    const bool lb = rb >= 0;
+    const unsigned char* sbase = ring + size_t(slot) * SLOT_BYTES;
+    // Row data of the factor threads' rows, loaded before the barrier.
+    const int frow = fh == 0 ? ra : rb;
+    float arow = 0.0f, u_old = 1.0f;
+    if (factor_thread && frow >= 0) {
+      arow = __ldg(p.a + frow);
+      u_old = __ldcg(p.U + frow);
+    }
+    float sa = 0.0f, sb = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      float fa[VE], fb[VE];
+      load_chunk(sbase, ra, k, fa);
+      if (lb) {
+        load_chunk(sbase + ROW_BYTES, rb, k, fb);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VE; ++e) fb[e] = 0.0f;
+      }
+#pragma unroll
+      for (int e = 0; e < VE; ++e) {
+        sa = fmaf(fa[e], V[k][e], sa);
+        sb = fmaf(fb[e], V[k][e], sb);
+      }
+    }
+    sa = warp_sum(sa);
+    sb = warp_sum(sb);
+    float* rq = red + (q & 1) * 2 * NW;
+    if (lane == 0) {
+      rq[warp] = sa;
+      rq[NW + warp] = sb;
+    }
+    if (__syncthreads_or(broken ? 1 : 0)) {
+      broken = true;
+      st |= DEV_TIMEOUT;
+      break;
+    }
+    float* uq = uf + (q & 1) * 2;
+    if (factor_thread && frow >= 0) {
+      float s_kv = 0.0f;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) s_kv += rq[fh * NW + w];
+      const float r = u_old * s_kv;
+      const float u_new = p.pot ? rescale_factor(arow * p.kscale, s_kv, p.fi, st) / p.kscale
+                                : u_old * rescale_factor(arow, r, p.fi, st) * gauge;
+      uq[fh] = u_new;
+      p.U[frow] = u_new;
+      if (p.track) {
+        auto kahan = [](float& sum, float& comp, float v) {
+          const float y = v - comp;
+          const float t2 = sum + y;
+          comp = (t2 - sum) - y;
+          sum = t2;
+        };
+        if (p.t >= 2) kahan(err_num, err_num_c, fabsf(r - p.r_prev[frow]));
+        kahan(err_den, err_den_c, r);
+        p.r_prev[frow] = r;
+      }
+    }
+    __syncthreads();
+    // The previous step's slot is no longer read by anyone (every thread has
+    // passed this barrier after its second read of it): refill it.
+    if (tid == 0 && q > 0) {
+      const int b2 = next_base;
+      arm(issued, b2);
+      ++issued;
+      if (b2 < n) next_base = atomicAdd(p.row_ctr, 2);
+    }
+    const float ua = uq[0], ub = lb ? uq[1] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      float fa[VE], fb[VE];
+      load_chunk(sbase, ra, k, fa);
+      if (lb) {
+        load_chunk(sbase + ROW_BYTES, rb, k, fb);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VE; ++e) fb[e] = 0.0f;
+      }
+#pragma unroll
+      for (int e = 0; e < VE; ++e) cacc[k][e] = fmaf(ub, fb[e], fmaf(ua, fa[e], cacc[k][e]));
+    }
+    ++done_steps;
+  }
+
+  if (done_steps > 0) {
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      const int cc = (k * THREADS + tid) * VE;
+      if (cc + VE <= m) {
+#pragma unroll
+        for (int e = 0; e < VE; e += 4)
+          red_add_v4(p.c_next + cc + e, cacc[k][e], cacc[k][e + 1], cacc[k][e + 2], cacc[k][e + 3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VE; ++e)
+          if (cc + e < m) atomicAdd(p.c_next + cc + e, cacc[k][e]);
+      }
+    }
+  }
+  if (p.track && factor_thread && done_steps > 0) {
+    atomicAdd(&p.err_next[0], double(err_num) - double(err_num_c));
+    atomicAdd(&p.err_next[1], double(err_den) - double(err_den_c));
+  }
+  if (st) atomicOr(&ctl->status, st);
+
+  // V_t for the next pass, once per column by the CTAs that finish last.
+  {
+    const int nsl = BETA_SLICES;
+    const int per = (m + nsl - 1) / nsl;
+    uint32_t st2 = 0;
+    finish_pass_job(p.arrive, p.slice_ctr, nsl, BETA_CTAS, HELP_LOOK_NS, [&](int sl) {
+      const int j0 = sl * per, j1 = min(m, j0 + per);
+      for (int j = j0 + tid; j < j1; j += THREADS) {
+        const float v = __ldcg(p.beta_out + j);
+        const float d = __ldcg(p.c_next + j);
+        const float c = v * d * inv_gauge;
+        p.beta_out[j] = p.pot ? rescale_factor(__ldg(p.b_ws + j), d, p.fi, st2)
+                              : v * rescale_factor(__ldg(p.b_ws + j), c, p.fi, st2) * inv_gauge;
+      }
+    });
+    if (st2) atomicOr(&ctl->status, st2);
+  }
+
+  if (tid == 0 && broken) {
+    for (int q = max(0, issued - stages); q < issued; ++q)
+      mbar_wait_bounded(&bars[q % stages], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS);
+  }
+}
+
+struct PairEntry {
+  int dtype, threads, kv;
+  const void* fn;
+};
+
+#define UOT_PAIR_ENTRY(T, DT, TH, KV) \
+  PairEntry { DT, TH, KV, reinterpret_cast<const void*>(&kform_pair_kernel<T, TH, KV>) }
+
+const PairEntry kPairTable[] = {
+    UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 512, 4), UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 256, 4),
+    UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 128, 4), UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 128, 2),
+    UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 64, 2),  UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 32, 2),
+    UOT_PAIR_ENTRY(__half, UOT_F16, 512, 4),         UOT_PAIR_ENTRY(__half, UOT_F16, 256, 4),
+    UOT_PAIR_ENTRY(__half, UOT_F16, 128, 4),         UOT_PAIR_ENTRY(__half, UOT_F16, 128, 2),
+    UOT_PAIR_ENTRY(__half, UOT_F16, 64, 2),          UOT_PAIR_ENTRY(__half, UOT_F16, 32, 2),
+};
+constexpr int kPairConfigs = int(sizeof(kPairTable) / sizeof(kPairTable[0]));
+
+size_t pair_smem(const PairEntry& e, int stages) {
+  const size_t row = size_t(e.kv) * 16 * e.threads;
+  return size_t(stages) * 2 * row + (4 * (e.threads / 32) + 4) * sizeof(float) +
+         size_t(stages) * 8 + size_t(stages) * 2 * sizeof(int);
+}
+
+std::mutex g_pair_mu;
+constexpr int PAIR_MAX_DEV = 64;
+size_t g_pair_smem_set[PAIR_MAX_DEV][kPairConfigs];
+struct PairGeo {
+  int dev, k, n, grid, stages;
+  size_t smem;
+};
+PairGeo g_pair_geo[32];
+int g_pair_geo_used = 0, g_pair_geo_next = 0;
+
+}  // namespace
+
+int kform_pair_pick(const FusedConfig& cfg) {
+  for (int i = 0; i < kPairConfigs; ++i)
+    if (kPairTable[i].dtype == cfg.dtype && kPairTable[i].threads == cfg.threads &&
+        kPairTable[i].kv == cfg.vecs)
+      return i;
+  return -1;
+}
+
+cudaError_t kform_pair_geometry(int i, int n, int* grid, int* stages, size_t* smem) {
+  const PairEntry& e = kPairTable[i];
+  int dev = 0, sms = 0, optin = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= PAIR_MAX_DEV) return cudaErrorInvalidDevice;
+  {
+    std::lock_guard<std::mutex> lock(g_pair_mu);
+    for (int j = 0; j < g_pair_geo_used; ++j)
+      if (g_pair_geo[j].dev == dev && g_pair_geo[j].k == i && g_pair_geo[j].n == n) {
+        *grid = g_pair_geo[j].grid;
+        *stages = g_pair_geo[j].stages;
+        *smem = g_pair_geo[j].smem;
+        return cudaSuccess;
+      }
+  }
+  err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (err != cudaSuccess) return err;
+  err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (err != cudaSuccess) return err;
+  // Deepest ring that keeps the CTA count per SM of a two-slot ring.
+  int occ2 = 0, best_s = 2;
+  for (int s = 2; s <= 8; ++s) {
+    const size_t b = pair_smem(e, s);
+    if (b > size_t(optin)) break;
+    {
+      std::lock_guard<std::mutex> lock(g_pair_mu);
+      if (g_pair_smem_set[dev][i] < b) {
+        err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b));
+        if (err != cudaSuccess) return err;
+        g_pair_smem_set[dev][i] = b;
+      }
+    }
+    int occ = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e.fn, e.threads, b);
+    if (err != cudaSuccess) return err;
+    if (s == 2) occ2 = occ;
+    if (occ < occ2 || occ == 0) break;
+    best_s = s;
+  }
+  if (occ2 == 0) return cudaErrorInvalidConfiguration;
+  *stages = best_s;
+  *smem = pair_smem(e, best_s);
+  int ctas = occ2 * sms;
+  const int cap = (n + 3) / 4;  // at least two pairs of rows per CTA
+  if (ctas > cap) ctas = cap > 0 ? cap : 1;
+  *grid = ctas;
+  std::lock_guard<std::mutex> lock(g_pair_mu);
+  const int slot = g_pair_geo_used < 32 ? g_pair_geo_used++ : (g_pair_geo_next++ % 32);
+  g_pair_geo[slot] = PairGeo{dev, i, n, *grid, *stages, *smem};
+  return cudaSuccess;
+}
+
+cudaError_t kform_pair_launch(int i, int grid, size_t smem, const FusedArgs& args, cudaStream_t s) {
+  const PairEntry& e = kPairTable[i];
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(e.threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  FusedArgs a = args;
+  void* kargs[] = {&a};
+  cudaError_t err = cudaLaunchKernelExC(&cfg, e.fn, kargs);
+  if (err == cudaSuccess) count_launch();
+  return err;
+}
+
+}  // namespace uot
