@@ -162,7 +162,16 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
   // Fused-pass geometry, validated before anything is enqueued.
   int k = -1, cs = 1, grid = 0, stages = 0, pair = -1;
   size_t smem = 0;
-  if (o.algo == UOT_ALGO_FUSED && iters > 0) {
+  const bool tma_ok = reinterpret_cast<uintptr_t>(mat) % 16 == 0 &&
+                      (uint64_t(ldm) * esize(o.dtype)) % 16 == 0;
+  // Kernel form with bulk copies and no forced configuration: two rows per
+  // step (kform_pair.cu).
+  if (kf && o.algo == UOT_ALGO_FUSED && iters > 0 && tma_ok && o.tile == 0 && o.cluster == 0)
+    pair = kform_pair_pick(o.dtype, m, &cs);
+  if (pair >= 0) {
+    if (kform_pair_geometry(pair, cs, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
+    if (o.max_ctas > 0 && grid > o.max_ctas) grid = std::max(cs, (o.max_ctas / cs) * cs);
+  } else if (o.algo == UOT_ALGO_FUSED && iters > 0) {
     k = fused_pick(o.dtype, m, o.tile);
     if (k < 0) return UOT_ERR_INVALID_ARG;
     FusedConfig cfg;
@@ -170,15 +179,7 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
     cs = o.cluster > 0 ? o.cluster : int((m + cfg.cols - 1) / cfg.cols);
     if (cs > 8) return UOT_ERR_UNSUPPORTED;
     if (int64_t(cs) * cfg.cols < m) return UOT_ERR_INVALID_ARG;
-    // 16-bit kernel form, one CTA per row, bulk copies: two rows per step.
-    const bool tma_ok = reinterpret_cast<uintptr_t>(mat) % 16 == 0 &&
-                        (uint64_t(ldm) * esize(o.dtype)) % 16 == 0;
-    if (kf && !hist && o.dtype != UOT_F32 && cs == 1 && tma_ok) pair = kform_pair_pick(cfg);
-    if (pair >= 0) {
-      if (kform_pair_geometry(pair, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
-    } else if (fused_geometry(kf, k, cs, N, &grid, &stages, &smem) != cudaSuccess) {
-      return UOT_ERR_CUDA;
-    }
+    if (fused_geometry(kf, k, cs, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
     if (o.max_ctas > 0 && grid > o.max_ctas) grid = std::max(cs, (o.max_ctas / cs) * cs);
   }
 
@@ -259,7 +260,7 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
         A.save_c = reinterpret_cast<float*>(hb + HL.c + size_t(t) * HL.strideV);
         A.save_V = reinterpret_cast<float*>(hb + HL.V + size_t(t) * HL.strideV);
       }
-      const cudaError_t le = pair >= 0 ? kform_pair_launch(pair, grid, smem, A, s)
+      const cudaError_t le = pair >= 0 ? kform_pair_launch(pair, cs, grid, smem, A, s)
                                        : fused_launch(kf, k, cs, grid, smem, tma, A, s);
       if (le != cudaSuccess) return UOT_ERR_CUDA;
     }

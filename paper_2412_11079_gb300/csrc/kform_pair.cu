@@ -1,22 +1,26 @@
-// Kernel-form pass over 16-bit K, two rows per step.
+// Kernel-form pass, two rows per step.
 //
 // The same iteration as fused_pass_kernel<T, ..., KF = true> (the plan kept
 // as diag(U) K diag(V), K read-only, FP32 scalings; one pass per iteration of
-// Section 2.1's rule, Algorithm 1's single sweep), for BF16/FP16 K when a row
-// fits one CTA and bulk copies apply.  A 16-bit row is half the bytes of an
-// FP32 row, so with one row per step the fixed latency of a step (barrier,
-// the row factor's power, the refill) bounds the pass well below HBM
-// bandwidth.  Here each step takes two consecutive rows: both row sums share
-// one barrier, two threads of the last warp form the two row factors, a
-// second barrier hands them to every thread, and the rows are read from
-// shared memory a second time for the column partials (holding two rows in
-// registers beside the column scalings and partial sums does not fit); the
-// slot is refilled after that second read.
+// Section 2.1's rule, Algorithm 1's single sweep) for K in FP32, BF16 or FP16
+// when bulk copies apply.  With one row per step the fixed latency of a step
+// (barrier, the row factor's power, the refill) bounds a read-only pass well
+// below HBM bandwidth.  Here each step takes two rows: both row sums share one
+// barrier, two threads of the last warp form the two row factors, a second
+// barrier hands them to every thread, and the rows are read from shared
+// memory a second time for the column partials (holding two rows in
+// registers beside the column scalings and partial sums does not fit); a
+// slot is refilled one step later, after that second read.
 //
-// Rows are taken in pairs from the pass's counter (the next pair fetched one
-// step ahead), alternating direction between passes; the column factors of
-// the next pass are formed by the CTAs that finish last (finish_pass_job).
-// The stopping rule's row sums are accumulated by the two factor threads.
+// A row wider than one CTA is split over a cluster of cs CTAs (CTA rank r on
+// columns [r W, (r+1) W)); the row partial sums go to every CTA of the
+// cluster through distributed shared memory before a cluster barrier, and
+// every CTA forms the same two factors.  With cs == 1 rows are taken in pairs
+// from the pass's counter (the next pair fetched one step ahead), alternating
+// direction between passes; clusters take pairs g, g + G, g + 2G, ...  The
+// column factors of the next pass are formed by the CTAs that finish last
+// (finish_pass_job).  The stopping rule's row sums are accumulated by the two
+// factor threads of rank 0; so is the adjoint's history when it is kept.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -27,24 +31,30 @@ namespace uot {
 
 namespace {
 
-template <typename T, int THREADS, int KV>
+template <typename T, int THREADS, int KV, bool CL>
 __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs p) {
   using E = Elem<T>;
-  constexpr int VE = E::VE;  // 8 elements per 16-byte vector
+  constexpr int VE = E::VE;  // elements per 16-byte vector
   constexpr int NW = THREADS / 32;
   constexpr int W = KV * VE * THREADS;
   constexpr int ROW_BYTES = W * int(sizeof(T));
   constexpr int SLOT_BYTES = 2 * ROW_BYTES;
+  constexpr int RQ = 2 * MAX_CLUSTER * NW;  // partials of one step: [row][rank][warp]
 
   extern __shared__ __align__(128) unsigned char smem[];
   const int stages = p.stages;
   unsigned char* ring = smem;
-  float* red = reinterpret_cast<float*>(smem + size_t(stages) * SLOT_BYTES);  // [2][2][NW]
-  float* uf = red + 4 * NW;                                                    // [2][2]
+  float* red = reinterpret_cast<float*>(smem + size_t(stages) * SLOT_BYTES);  // [2][RQ]
+  float* uf = red + 2 * RQ;                                                    // [2][2]
   uint64_t* bars = reinterpret_cast<uint64_t*>(uf + 4);
   int* slot_rows = reinterpret_cast<int*>(bars + stages);  // [stages][2]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // CL: launched in clusters (a row split over cs CTAs).
+  const uint32_t cs = CL ? cluster_nctarank() : 1u;
+  const uint32_t cr = CL ? cluster_ctarank() : 0u;
+  const int cid = CL ? int(cluster_id_x()) : int(blockIdx.x);
+  const int ncl = CL ? int(ncluster_x()) : int(gridDim.x);
   Control* ctl = p.ctl;
   if (p.track) {
     if (*reinterpret_cast<volatile int32_t*>(&ctl->done)) return;
@@ -63,18 +73,22 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
   }
 
   const int m = p.m, n = p.n;
+  const int col0 = int(cr) * W;
   float gauge = 1.0f, inv_gauge = 1.0f;
   {
     const int e = gauge_exponent(p.t, float(*p.log2k));
     gauge = ldexpf(1.0f, e);
     inv_gauge = ldexpf(1.0f, -e);
   }
-  const int valid = min(W, m);
+  const int valid = max(0, min(W, m - col0));
   const uint32_t copy_bytes = uint32_t((size_t(valid) * sizeof(T)) & ~size_t(15));
   const T* plan = reinterpret_cast<const T*>(p.plan);
   const int64_t ldp = p.ldp;
   uint32_t st = 0;
   const uint64_t policy = policy_evict_first();
+  const bool dyn = !CL;
+  const int npairs = (n + 1) / 2;
+  const int nq = cid < npairs ? (npairs - 1 - cid) / ncl + 1 : 0;  // static pairs
   int issued = 0, next_base = n;
 
   if (tid == 0) {
@@ -82,13 +96,14 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
     fence_mbar_init();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  __syncthreads();
+  // All CTAs of the cluster run before distributed shared memory is written.
+  if constexpr (CL) cluster_sync(); else __syncthreads();
 
-  const bool flip = (p.t & 1) == 0;
+  const bool flip = dyn && (p.t & 1) == 0;
   // Arms the slot of step q with the rows base, base + 1 (those below n).
   auto arm = [&](int q, int base) {
     const int slot = q % stages;
-    if (base < n) {
+    if (base >= 0 && base < n) {
       int ra = base, rb = base + 1 < n ? base + 1 : -1;
       if (flip) {
         ra = n - 1 - ra;
@@ -98,10 +113,10 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
       slot_rows[2 * slot + 1] = rb;
       if (copy_bytes) {
         mbar_arrive_expect_tx(&bars[slot], copy_bytes * (rb >= 0 ? 2u : 1u));
-        bulk_load(ring + size_t(slot) * SLOT_BYTES, plan + int64_t(ra) * ldp, copy_bytes,
+        bulk_load(ring + size_t(slot) * SLOT_BYTES, plan + int64_t(ra) * ldp + col0, copy_bytes,
                   &bars[slot], policy);
         if (rb >= 0)
-          bulk_load(ring + size_t(slot) * SLOT_BYTES + ROW_BYTES, plan + int64_t(rb) * ldp,
+          bulk_load(ring + size_t(slot) * SLOT_BYTES + ROW_BYTES, plan + int64_t(rb) * ldp + col0,
                     copy_bytes, &bars[slot], policy);
       } else {
         mbar_arrive(&bars[slot]);
@@ -111,18 +126,23 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
       mbar_arrive(&bars[slot]);
     }
   };
+  auto static_base = [&](int q) { return q < nq ? 2 * (cid + q * ncl) : -1; };
   if (tid == 0) {
-    const int base = atomicAdd(p.row_ctr, 2 * stages);
-    for (int q = 0; q < stages; ++q) arm(q, base + 2 * q);
+    if (dyn) {
+      const int base = atomicAdd(p.row_ctr, 2 * stages);
+      for (int q = 0; q < stages; ++q) arm(q, base + 2 * q);
+      if (base + 2 * stages < n) next_base = atomicAdd(p.row_ctr, 2);
+    } else {
+      for (int q = 0; q < stages; ++q) arm(q, static_base(q));
+    }
     issued = stages;
-    if (base + 2 * stages < n) next_base = atomicAdd(p.row_ctr, 2);
   }
 
   // Column scalings V of this thread's columns (zero-padded buffer).
   float V[KV][VE];
 #pragma unroll
   for (int k = 0; k < KV; ++k) {
-    const int cc = (k * THREADS + tid) * VE;
+    const int cc = col0 + (k * THREADS + tid) * VE;
     if (cc < m) {
 #pragma unroll
       for (int e = 0; e < VE; e += 4) {
@@ -155,12 +175,13 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
   // step, THREADS-2 for the second.
   const int fh = THREADS - 1 - tid;  // 0 or 1 for the factor threads
   const bool factor_thread = fh == 0 || fh == 1;
+  const bool writer = factor_thread && cr == 0;  // U, history and stopping sums
   float err_num = 0.0f, err_den = 0.0f, err_num_c = 0.0f, err_den_c = 0.0f;
   bool broken = false;
   int done_steps = 0;
 
-  // Packed row chunk k of a row (bulk-copied part from the slot, the rest
-  // from global memory, columns >= m as zeros).
+  // Chunk k of a row as FP32: the bulk-copied part from the slot, the rest
+  // from global memory, columns >= m as zeros.
   auto load_chunk = [&](const unsigned char* srow, int row, int k, float (&f)[VE]) {
     const int li = k * THREADS + tid;
     const int cc = li * VE;
@@ -168,11 +189,13 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
       E::unpack(ld_shared_v4(srow + size_t(li) * 16), f);
     } else {
 #pragma unroll
-      for (int e = 0; e < VE; ++e) f[e] = (cc + e < m) ? E::load1(plan + int64_t(row) * ldp + cc + e) : 0.0f;
+      for (int e = 0; e < VE; ++e)
+        f[e] = (col0 + cc + e < m) ? E::load1(plan + int64_t(row) * ldp + col0 + cc + e) : 0.0f;
     }
   };
 
   for (int q = 0;; ++q) {
+    if (CL && q >= nq) break;
     const int slot = q % stages;
     if (!broken && !mbar_wait_bounded(&bars[slot], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS)) {
       broken = true;
@@ -209,12 +232,21 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
     }
     sa = warp_sum(sa);
     sb = warp_sum(sb);
-    float* rq = red + (q & 1) * 2 * NW;
+    float* rq = red + (q & 1) * RQ;
     if (lane == 0) {
-      rq[warp] = sa;
-      rq[NW + warp] = sb;
+      if constexpr (!CL) {
+        rq[warp] = sa;
+        rq[MAX_CLUSTER * NW + warp] = sb;
+      } else {
+        for (uint32_t r = 0; r < cs; ++r) {
+          st_cluster_f32(map_shared_rank(rq + cr * NW + warp, r), sa);
+          st_cluster_f32(map_shared_rank(rq + (MAX_CLUSTER + cr) * NW + warp, r), sb);
+        }
+      }
     }
-    if (__syncthreads_or(broken ? 1 : 0)) {
+    if constexpr (CL) {
+      cluster_sync();  // static pairs: the loop is bounded by nq
+    } else if (__syncthreads_or(broken ? 1 : 0)) {
       broken = true;
       st |= DEV_TIMEOUT;
       break;
@@ -222,33 +254,49 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
     float* uq = uf + (q & 1) * 2;
     if (factor_thread && frow >= 0) {
       float s_kv = 0.0f;
+      if constexpr (!CL) {
 #pragma unroll
-      for (int w = 0; w < NW; ++w) s_kv += rq[fh * NW + w];
-      const float r = u_old * s_kv;
+        for (int w = 0; w < NW; ++w) s_kv += rq[fh * MAX_CLUSTER * NW + w];
+      } else {
+        for (uint32_t r = 0; r < cs; ++r)
+#pragma unroll
+          for (int w = 0; w < NW; ++w) s_kv += rq[(fh * MAX_CLUSTER + int(r)) * NW + w];
+      }
+      const float rsum = u_old * s_kv;
       const float u_new = p.pot ? rescale_factor(arow * p.kscale, s_kv, p.fi, st) / p.kscale
-                                : u_old * rescale_factor(arow, r, p.fi, st) * gauge;
+                                : u_old * rescale_factor(arow, rsum, p.fi, st) * gauge;
       uq[fh] = u_new;
-      p.U[frow] = u_new;
-      if (p.track) {
-        auto kahan = [](float& sum, float& comp, float v) {
-          const float y = v - comp;
-          const float t2 = sum + y;
-          comp = (t2 - sum) - y;
-          sum = t2;
-        };
-        if (p.t >= 2) kahan(err_num, err_num_c, fabsf(r - p.r_prev[frow]));
-        kahan(err_den, err_den_c, r);
-        p.r_prev[frow] = r;
+      if (writer) {
+        p.U[frow] = u_new;
+        if (p.save_r) {  // history for the adjoint: r_t and U_t of this row
+          p.save_r[frow] = rsum;
+          p.save_U[frow] = u_new;
+        }
+        if (p.track) {
+          auto kahan = [](float& sum, float& comp, float v) {
+            const float y = v - comp;
+            const float t2 = sum + y;
+            comp = (t2 - sum) - y;
+            sum = t2;
+          };
+          if (p.t >= 2) kahan(err_num, err_num_c, fabsf(rsum - p.r_prev[frow]));
+          kahan(err_den, err_den_c, rsum);
+          p.r_prev[frow] = rsum;
+        }
       }
     }
     __syncthreads();
-    // The previous step's slot is no longer read by anyone (every thread has
-    // passed this barrier after its second read of it): refill it.
+    // The previous step's slot is no longer read by anyone (every thread of
+    // this CTA has passed this barrier after its second read of it): refill.
     if (tid == 0 && q > 0) {
-      const int b2 = next_base;
-      arm(issued, b2);
+      if (dyn) {
+        const int b2 = next_base;
+        arm(issued, b2);
+        if (b2 < n) next_base = atomicAdd(p.row_ctr, 2);
+      } else {
+        arm(issued, static_base(issued));
+      }
       ++issued;
-      if (b2 < n) next_base = atomicAdd(p.row_ctr, 2);
     }
     const float ua = uq[0], ub = lb ? uq[1] : 0.0f;
 #pragma unroll
@@ -270,7 +318,7 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
   if (done_steps > 0) {
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
-      const int cc = (k * THREADS + tid) * VE;
+      const int cc = col0 + (k * THREADS + tid) * VE;
       if (cc + VE <= m) {
 #pragma unroll
         for (int e = 0; e < VE; e += 4)
@@ -282,7 +330,7 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
       }
     }
   }
-  if (p.track && factor_thread && done_steps > 0) {
+  if (p.track && writer && done_steps > 0) {
     atomicAdd(&p.err_next[0], double(err_num) - double(err_num_c));
     atomicAdd(&p.err_next[1], double(err_den) - double(err_den_c));
   }
@@ -299,8 +347,13 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
         const float v = __ldcg(p.beta_out + j);
         const float d = __ldcg(p.c_next + j);
         const float c = v * d * inv_gauge;
-        p.beta_out[j] = p.pot ? rescale_factor(__ldg(p.b_ws + j), d, p.fi, st2)
-                              : v * rescale_factor(__ldg(p.b_ws + j), c, p.fi, st2) * inv_gauge;
+        const float v_new = p.pot ? rescale_factor(__ldg(p.b_ws + j), d, p.fi, st2)
+                                  : v * rescale_factor(__ldg(p.b_ws + j), c, p.fi, st2) * inv_gauge;
+        p.beta_out[j] = v_new;
+        if (p.save_c) {  // history for the adjoint: c_t and V_t of this column
+          p.save_c[j] = c;
+          p.save_V[j] = v_new;
+        }
       }
     });
     if (st2) atomicOr(&ctl->status, st2);
@@ -314,13 +367,21 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
 
 struct PairEntry {
   int dtype, threads, kv;
-  const void* fn;
+  const void* fn;     // one CTA per row
+  const void* fn_cl;  // rows split over a cluster
 };
 
-#define UOT_PAIR_ENTRY(T, DT, TH, KV) \
-  PairEntry { DT, TH, KV, reinterpret_cast<const void*>(&kform_pair_kernel<T, TH, KV>) }
+#define UOT_PAIR_ENTRY(T, DT, TH, KV)                                            \
+  PairEntry {                                                                    \
+    DT, TH, KV, reinterpret_cast<const void*>(&kform_pair_kernel<T, TH, KV, false>), \
+        reinterpret_cast<const void*>(&kform_pair_kernel<T, TH, KV, true>)         \
+  }
 
+// Configurations whose two-row slot leaves room for a ring of three.
 const PairEntry kPairTable[] = {
+    UOT_PAIR_ENTRY(float, UOT_F32, 512, 4),          UOT_PAIR_ENTRY(float, UOT_F32, 256, 4),
+    UOT_PAIR_ENTRY(float, UOT_F32, 128, 4),          UOT_PAIR_ENTRY(float, UOT_F32, 128, 2),
+    UOT_PAIR_ENTRY(float, UOT_F32, 64, 2),           UOT_PAIR_ENTRY(float, UOT_F32, 32, 2),
     UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 512, 4), UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 256, 4),
     UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 128, 4), UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 128, 2),
     UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 64, 2),  UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 32, 2),
@@ -332,31 +393,68 @@ constexpr int kPairConfigs = int(sizeof(kPairTable) / sizeof(kPairTable[0]));
 
 size_t pair_smem(const PairEntry& e, int stages) {
   const size_t row = size_t(e.kv) * 16 * e.threads;
-  return size_t(stages) * 2 * row + (4 * (e.threads / 32) + 4) * sizeof(float) +
+  return size_t(stages) * 2 * row + (2 * 2 * MAX_CLUSTER * (e.threads / 32) + 4) * sizeof(float) +
          size_t(stages) * 8 + size_t(stages) * 2 * sizeof(int);
+}
+
+int pair_cols(const PairEntry& e) {
+  return e.threads * e.kv * (e.dtype == UOT_F32 ? 4 : 8);
 }
 
 std::mutex g_pair_mu;
 constexpr int PAIR_MAX_DEV = 64;
-size_t g_pair_smem_set[PAIR_MAX_DEV][kPairConfigs];
+size_t g_pair_smem_set[PAIR_MAX_DEV][kPairConfigs][2];
+bool g_pair_cluster_set[PAIR_MAX_DEV][kPairConfigs];
 struct PairGeo {
-  int dev, k, n, grid, stages;
+  int dev, k, cs, n, grid, stages;
   size_t smem;
 };
 PairGeo g_pair_geo[32];
 int g_pair_geo_used = 0, g_pair_geo_next = 0;
 
-}  // namespace
-
-int kform_pair_pick(const FusedConfig& cfg) {
-  for (int i = 0; i < kPairConfigs; ++i)
-    if (kPairTable[i].dtype == cfg.dtype && kPairTable[i].threads == cfg.threads &&
-        kPairTable[i].kv == cfg.vecs)
-      return i;
-  return -1;
+cudaError_t pair_attributes(int dev, int i, size_t smem, bool cluster) {
+  const PairEntry& e = kPairTable[i];
+  const void* fn = cluster ? e.fn_cl : e.fn;
+  std::lock_guard<std::mutex> lock(g_pair_mu);
+  if (g_pair_smem_set[dev][i][cluster] < smem) {
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (err != cudaSuccess) return err;
+    g_pair_smem_set[dev][i][cluster] = smem;
+  }
+  if (cluster && !g_pair_cluster_set[dev][i]) {
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (err != cudaSuccess) return err;
+    g_pair_cluster_set[dev][i] = true;
+  }
+  return cudaSuccess;
 }
 
-cudaError_t kform_pair_geometry(int i, int n, int* grid, int* stages, size_t* smem) {
+}  // namespace
+
+int kform_pair_pick(int dtype, int64_t m, int* cs) {
+  // The narrowest configuration that covers the row, else the widest one
+  // split over a cluster.
+  int best = -1, widest = -1;
+  for (int i = 0; i < kPairConfigs; ++i) {
+    const PairEntry& e = kPairTable[i];
+    if (e.dtype != dtype) continue;
+    if (widest < 0 || pair_cols(e) > pair_cols(kPairTable[widest])) widest = i;
+    if (pair_cols(e) >= m && (best < 0 || pair_cols(e) < pair_cols(kPairTable[best]))) best = i;
+  }
+  if (best >= 0) {
+    *cs = 1;
+    return best;
+  }
+  // Wider FP32 rows measured faster with the one-row pass of 16384 columns
+  // per CTA than split over clusters of two-row CTAs of 8192.
+  if (widest < 0 || dtype == UOT_F32) return -1;
+  const int64_t c = (m + pair_cols(kPairTable[widest]) - 1) / pair_cols(kPairTable[widest]);
+  if (c > MAX_CLUSTER) return -1;
+  *cs = int(c);
+  return widest;
+}
+
+cudaError_t kform_pair_geometry(int i, int cs, int n, int* grid, int* stages, size_t* smem) {
   const PairEntry& e = kPairTable[i];
   int dev = 0, sms = 0, optin = 0;
   cudaError_t err = cudaGetDevice(&dev);
@@ -364,13 +462,15 @@ cudaError_t kform_pair_geometry(int i, int n, int* grid, int* stages, size_t* sm
   if (dev < 0 || dev >= PAIR_MAX_DEV) return cudaErrorInvalidDevice;
   {
     std::lock_guard<std::mutex> lock(g_pair_mu);
-    for (int j = 0; j < g_pair_geo_used; ++j)
-      if (g_pair_geo[j].dev == dev && g_pair_geo[j].k == i && g_pair_geo[j].n == n) {
-        *grid = g_pair_geo[j].grid;
-        *stages = g_pair_geo[j].stages;
-        *smem = g_pair_geo[j].smem;
+    for (int j = 0; j < g_pair_geo_used; ++j) {
+      const PairGeo& g = g_pair_geo[j];
+      if (g.dev == dev && g.k == i && g.cs == cs && g.n == n) {
+        *grid = g.grid;
+        *stages = g.stages;
+        *smem = g.smem;
         return cudaSuccess;
       }
+    }
   }
   err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (err != cudaSuccess) return err;
@@ -381,16 +481,10 @@ cudaError_t kform_pair_geometry(int i, int n, int* grid, int* stages, size_t* sm
   for (int s = 2; s <= 8; ++s) {
     const size_t b = pair_smem(e, s);
     if (b > size_t(optin)) break;
-    {
-      std::lock_guard<std::mutex> lock(g_pair_mu);
-      if (g_pair_smem_set[dev][i] < b) {
-        err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b));
-        if (err != cudaSuccess) return err;
-        g_pair_smem_set[dev][i] = b;
-      }
-    }
+    err = pair_attributes(dev, i, b, cs > 1);
+    if (err != cudaSuccess) return err;
     int occ = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e.fn, e.threads, b);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cs > 1 ? e.fn_cl : e.fn, e.threads, b);
     if (err != cudaSuccess) return err;
     if (s == 2) occ2 = occ;
     if (occ < occ2 || occ == 0) break;
@@ -399,26 +493,54 @@ cudaError_t kform_pair_geometry(int i, int n, int* grid, int* stages, size_t* sm
   if (occ2 == 0) return cudaErrorInvalidConfiguration;
   *stages = best_s;
   *smem = pair_smem(e, best_s);
-  int ctas = occ2 * sms;
-  const int cap = (n + 3) / 4;  // at least two pairs of rows per CTA
-  if (ctas > cap) ctas = cap > 0 ? cap : 1;
-  *grid = ctas;
+  int clusters = occ2 * sms;
+  if (cs > 1) {
+    err = pair_attributes(dev, i, *smem, true);
+    if (err != cudaSuccess) return err;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs * occ2 * sms, 1, 1);
+    cfg.blockDim = dim3(e.threads, 1, 1);
+    cfg.dynamicSmemBytes = *smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    err = cudaOccupancyMaxActiveClusters(&nc, e.fn_cl, &cfg);
+    if (err != cudaSuccess) return err;
+    if (nc <= 0) return cudaErrorInvalidConfiguration;
+    clusters = nc;
+  }
+  const int cap = (n + 3) / 4;  // at least two pairs of rows per cluster
+  if (clusters > cap) clusters = cap > 0 ? cap : 1;
+  *grid = clusters * cs;
   std::lock_guard<std::mutex> lock(g_pair_mu);
   const int slot = g_pair_geo_used < 32 ? g_pair_geo_used++ : (g_pair_geo_next++ % 32);
-  g_pair_geo[slot] = PairGeo{dev, i, n, *grid, *stages, *smem};
+  g_pair_geo[slot] = PairGeo{dev, i, cs, n, *grid, *stages, *smem};
   return cudaSuccess;
 }
 
-cudaError_t kform_pair_launch(int i, int grid, size_t smem, const FusedArgs& args, cudaStream_t s) {
+cudaError_t kform_pair_launch(int i, int cs, int grid, size_t smem, const FusedArgs& args,
+                              cudaStream_t s) {
   const PairEntry& e = kPairTable[i];
   cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(grid, 1, 1);
   cfg.blockDim = dim3(e.threads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = cs > 1 ? 1 : 0;
   FusedArgs a = args;
   void* kargs[] = {&a};
-  cudaError_t err = cudaLaunchKernelExC(&cfg, e.fn, kargs);
+  cudaError_t err = cudaLaunchKernelExC(&cfg, cs > 1 ? e.fn_cl : e.fn, kargs);
   if (err == cudaSuccess) count_launch();
   return err;
 }

@@ -179,12 +179,12 @@ cudaError_t launch_multipass_iter(void* P, int64_t ldp, int n, int m, int dtype,
 cudaError_t launch_hist_init(uint8_t* hist, int n, int m, int iters, float u0, const double* log2k,
                              cudaStream_t s);
 
-// Kernel-form pass over 16-bit K with two rows per step (kform_pair.cu):
-// the pair configuration matching fused configuration `cfg` (-1 if none),
-// its launch geometry for n rows, and one launch.
-int kform_pair_pick(const FusedConfig& cfg);
-cudaError_t kform_pair_geometry(int pair, int n, int* grid, int* stages, size_t* smem);
-cudaError_t kform_pair_launch(int pair, int grid, size_t smem, const FusedArgs& args,
+// Kernel-form pass with two rows per step (kform_pair.cu): the configuration
+// for rows of m columns of `dtype` and its cluster size (-1 if none), its
+// launch geometry for n rows, and one launch.
+int kform_pair_pick(int dtype, int64_t m, int* cs);
+cudaError_t kform_pair_geometry(int pair, int cs, int n, int* grid, int* stages, size_t* smem);
+cudaError_t kform_pair_launch(int pair, int cs, int grid, size_t smem, const FusedArgs& args,
                               cudaStream_t s);
 
 void count_launch(int k = 1);
