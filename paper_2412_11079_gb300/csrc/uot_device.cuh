@@ -297,10 +297,6 @@ __device__ __forceinline__ void st_cluster_v4(uint32_t addr, const float4& v) {
 __device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v) {
   asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
-// Barrier `id` (1..15) over `nthreads` threads (a multiple of 32) of the CTA.
-__device__ __forceinline__ void named_barrier(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
