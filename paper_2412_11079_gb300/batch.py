@@ -84,7 +84,7 @@ def candidates():
     for stages in (2, 3):
         for max_team in (16, 32, 64):
             for target in (1.0e7, 4.0e7):
-                for cluster in (8, 16):
+                for cluster in (4, 8, 16):
                     out.append(uot.batch_tuning(stages, max_team, target, cluster))
     return out
 
