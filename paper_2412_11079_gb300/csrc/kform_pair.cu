@@ -6,11 +6,14 @@
 // when bulk copies apply.  With one row per step the fixed latency of a step
 // (barrier, the row factor's power, the refill) bounds a read-only pass well
 // below HBM bandwidth.  Here each step takes two rows: both row sums share one
-// barrier, two threads of the last warp form the two row factors, a second
-// barrier hands them to every thread, and the rows are read from shared
-// memory a second time for the column partials (holding two rows in
-// registers beside the column scalings and partial sums does not fit); a
-// slot is refilled one step later, after that second read.
+// barrier, two threads of the last warp form the two row factors, and a
+// second barrier hands them to every thread.  With HOLD each thread keeps
+// its part of both rows in registers as packed 16-byte vectors for the
+// column partials, so the first barrier already shows the slot fully read and
+// it is refilled at once: every slot of the ring is loading while a step
+// computes.  Without HOLD (where those registers would spill) the rows are
+// read from shared memory a second time and a slot is refilled one step
+// later, so one slot of the ring is held through each step.
 //
 // A row wider than one CTA is split over a cluster of cs CTAs (CTA rank r on
 // columns [r W, (r+1) W)); the row partial sums go to every CTA of the
@@ -31,7 +34,7 @@ namespace uot {
 
 namespace {
 
-template <typename T, int THREADS, int KV, bool CL>
+template <typename T, int THREADS, int KV, bool CL, bool HOLD>
 __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs p) {
   using E = Elem<T>;
   constexpr int VE = E::VE;  // elements per 16-byte vector
@@ -180,18 +183,17 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
   bool broken = false;
   int done_steps = 0;
 
-  // Chunk k of a row as FP32: the bulk-copied part from the slot, the rest
-  // from global memory, columns >= m as zeros.
-  auto load_chunk = [&](const unsigned char* srow, int row, int k, float (&f)[VE]) {
+  // Chunk k of a row as a packed 16-byte vector: the bulk-copied part from
+  // the slot, the rest from global memory, columns >= m as zeros.
+  auto load_raw = [&](const unsigned char* srow, int row, int k) -> uint4 {
     const int li = k * THREADS + tid;
     const int cc = li * VE;
-    if ((cc + VE) * int(sizeof(T)) <= int(copy_bytes)) {
-      E::unpack(ld_shared_v4(srow + size_t(li) * 16), f);
-    } else {
+    if ((cc + VE) * int(sizeof(T)) <= int(copy_bytes)) return ld_shared_v4(srow + size_t(li) * 16);
+    float f[VE];
 #pragma unroll
-      for (int e = 0; e < VE; ++e)
-        f[e] = (col0 + cc + e < m) ? E::load1(plan + int64_t(row) * ldp + col0 + cc + e) : 0.0f;
-    }
+    for (int e = 0; e < VE; ++e)
+      f[e] = (col0 + cc + e < m) ? E::load1(plan + int64_t(row) * ldp + col0 + cc + e) : 0.0f;
+    return E::pack(f);  // exact: the values are elements of T
   };
 
   for (int q = 0;; ++q) {
@@ -213,17 +215,18 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
       arow = __ldg(p.a + frow);
       u_old = __ldcg(p.U + frow);
     }
+    uint4 xa[KV], xb[KV];
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      xa[k] = load_raw(sbase, ra, k);
+      xb[k] = lb ? load_raw(sbase + ROW_BYTES, rb, k) : make_uint4(0u, 0u, 0u, 0u);
+    }
     float sa = 0.0f, sb = 0.0f;
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
       float fa[VE], fb[VE];
-      load_chunk(sbase, ra, k, fa);
-      if (lb) {
-        load_chunk(sbase + ROW_BYTES, rb, k, fb);
-      } else {
-#pragma unroll
-        for (int e = 0; e < VE; ++e) fb[e] = 0.0f;
-      }
+      E::unpack(xa[k], fa);
+      E::unpack(xb[k], fb);
 #pragma unroll
       for (int e = 0; e < VE; ++e) {
         sa = fmaf(fa[e], V[k][e], sa);
@@ -251,6 +254,19 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
       st |= DEV_TIMEOUT;
       break;
     }
+    auto refill = [&]() {
+      if (dyn) {
+        const int b2 = next_base;
+        arm(issued, b2);
+        if (b2 < n) next_base = atomicAdd(p.row_ctr, 2);
+      } else {
+        arm(issued, static_base(issued));
+      }
+      ++issued;
+    };
+    // HOLD: every thread of this CTA has its part of this step's rows in
+    // registers (their sums are posted), so the slot is free.
+    if (HOLD && tid == 0) refill();
     float* uq = uf + (q & 1) * 2;
     if (factor_thread && frow >= 0) {
       float s_kv = 0.0f;
@@ -286,28 +302,19 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
       }
     }
     __syncthreads();
-    // The previous step's slot is no longer read by anyone (every thread of
-    // this CTA has passed this barrier after its second read of it): refill.
-    if (tid == 0 && q > 0) {
-      if (dyn) {
-        const int b2 = next_base;
-        arm(issued, b2);
-        if (b2 < n) next_base = atomicAdd(p.row_ctr, 2);
-      } else {
-        arm(issued, static_base(issued));
-      }
-      ++issued;
-    }
+    // Without HOLD the previous step's slot is no longer read by anyone
+    // (every thread has passed this barrier after its second read of it).
+    if (!HOLD && tid == 0 && q > 0) refill();
     const float ua = uq[0], ub = lb ? uq[1] : 0.0f;
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
       float fa[VE], fb[VE];
-      load_chunk(sbase, ra, k, fa);
-      if (lb) {
-        load_chunk(sbase + ROW_BYTES, rb, k, fb);
+      if constexpr (HOLD) {
+        E::unpack(xa[k], fa);
+        E::unpack(xb[k], fb);
       } else {
-#pragma unroll
-        for (int e = 0; e < VE; ++e) fb[e] = 0.0f;
+        E::unpack(load_raw(sbase, ra, k), fa);
+        E::unpack(lb ? load_raw(sbase + ROW_BYTES, rb, k) : make_uint4(0u, 0u, 0u, 0u), fb);
       }
 #pragma unroll
       for (int e = 0; e < VE; ++e) cacc[k][e] = fmaf(ub, fb[e], fmaf(ua, fa[e], cacc[k][e]));
@@ -371,23 +378,37 @@ struct PairEntry {
   const void* fn_cl;  // rows split over a cluster
 };
 
-#define UOT_PAIR_ENTRY(T, DT, TH, KV)                                            \
-  PairEntry {                                                                    \
-    DT, TH, KV, reinterpret_cast<const void*>(&kform_pair_kernel<T, TH, KV, false>), \
-        reinterpret_cast<const void*>(&kform_pair_kernel<T, TH, KV, true>)         \
+#define UOT_PAIR_ENTRY(T, DT, TH, KV, H)                                                \
+  PairEntry {                                                                           \
+    DT, TH, KV, reinterpret_cast<const void*>(&kform_pair_kernel<T, TH, KV, false, H>), \
+        reinterpret_cast<const void*>(&kform_pair_kernel<T, TH, KV, true, H>)             \
   }
 
-// Configurations whose two-row slot leaves room for a ring of three.
+// Configurations whose two-row slot leaves room for a ring of three.  Rows
+// are held in registers (HOLD) except in the 16-bit configuration of 16384
+// columns, where V, the column partials and two rows would need more than
+// the 128 registers a thread of a 512-thread CTA may have.
+// 16-bit rows of up to 8192 columns take 512 x 2 with HOLD (45 us per pass
+// at 8192^2, against 65 us for 256 x 4 re-reading its rows).
 const PairEntry kPairTable[] = {
-    UOT_PAIR_ENTRY(float, UOT_F32, 512, 4),          UOT_PAIR_ENTRY(float, UOT_F32, 256, 4),
-    UOT_PAIR_ENTRY(float, UOT_F32, 128, 4),          UOT_PAIR_ENTRY(float, UOT_F32, 128, 2),
-    UOT_PAIR_ENTRY(float, UOT_F32, 64, 2),           UOT_PAIR_ENTRY(float, UOT_F32, 32, 2),
-    UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 512, 4), UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 256, 4),
-    UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 128, 4), UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 128, 2),
-    UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 64, 2),  UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 32, 2),
-    UOT_PAIR_ENTRY(__half, UOT_F16, 512, 4),         UOT_PAIR_ENTRY(__half, UOT_F16, 256, 4),
-    UOT_PAIR_ENTRY(__half, UOT_F16, 128, 4),         UOT_PAIR_ENTRY(__half, UOT_F16, 128, 2),
-    UOT_PAIR_ENTRY(__half, UOT_F16, 64, 2),          UOT_PAIR_ENTRY(__half, UOT_F16, 32, 2),
+    UOT_PAIR_ENTRY(float, UOT_F32, 512, 4, true),
+    UOT_PAIR_ENTRY(float, UOT_F32, 256, 4, true),
+    UOT_PAIR_ENTRY(float, UOT_F32, 128, 4, true),
+    UOT_PAIR_ENTRY(float, UOT_F32, 128, 2, true),
+    UOT_PAIR_ENTRY(float, UOT_F32, 64, 2, true),
+    UOT_PAIR_ENTRY(float, UOT_F32, 32, 2, true),
+    UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 512, 4, false),
+    UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 512, 2, true),
+    UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 128, 4, true),
+    UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 128, 2, true),
+    UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 64, 2, true),
+    UOT_PAIR_ENTRY(__nv_bfloat16, UOT_BF16, 32, 2, true),
+    UOT_PAIR_ENTRY(__half, UOT_F16, 512, 4, false),
+    UOT_PAIR_ENTRY(__half, UOT_F16, 512, 2, true),
+    UOT_PAIR_ENTRY(__half, UOT_F16, 128, 4, true),
+    UOT_PAIR_ENTRY(__half, UOT_F16, 128, 2, true),
+    UOT_PAIR_ENTRY(__half, UOT_F16, 64, 2, true),
+    UOT_PAIR_ENTRY(__half, UOT_F16, 32, 2, true),
 };
 constexpr int kPairConfigs = int(sizeof(kPairTable) / sizeof(kPairTable[0]));
 
@@ -446,7 +467,9 @@ int kform_pair_pick(int dtype, int64_t m, int* cs) {
     return best;
   }
   // Wider FP32 rows measured faster with the one-row pass of 16384 columns
-  // per CTA than split over clusters of two-row CTAs of 8192.
+  // per CTA than split over clusters of two-row CTAs of 8192; wider 16-bit
+  // rows faster over clusters of the 16384-column configuration than of the
+  // 8192-column one that holds its rows (540 against 833 us at 32768^2).
   if (widest < 0 || dtype == UOT_F32) return -1;
   const int64_t c = (m + pair_cols(kPairTable[widest]) - 1) / pair_cols(kPairTable[widest]);
   if (c > MAX_CLUSTER) return -1;
