@@ -103,6 +103,12 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
   if constexpr (CL) cluster_sync(); else __syncthreads();
 
   const bool flip = dyn && (p.t & 1) == 0;
+  // Whole rows stored back to back: a step's two rows (adjacent, the lower
+  // first) come in one bulk copy, and the second row follows the first in
+  // the slot.  A bulk copy has a fixed cost of about 0.3 us on an SM's copy
+  // engine, which caps copies of one 8 KB row each at ~27 GB/s per SM.
+  const bool joint = !CL && size_t(m) * sizeof(T) == copy_bytes && ldp == m;
+  const uint32_t rowb_off = joint ? copy_bytes : uint32_t(ROW_BYTES);
   // Arms the slot of step q with the rows base, base + 1 (those below n).
   auto arm = [&](int q, int base) {
     const int slot = q % stages;
@@ -110,16 +116,23 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
       int ra = base, rb = base + 1 < n ? base + 1 : -1;
       if (flip) {
         ra = n - 1 - ra;
-        if (rb >= 0) rb = n - 1 - rb;
+        if (rb >= 0) {  // keep the lower row first
+          rb = ra;
+          ra = ra - 1;
+        }
       }
       slot_rows[2 * slot] = ra;
       slot_rows[2 * slot + 1] = rb;
-      if (copy_bytes) {
+      if (copy_bytes && joint && rb >= 0) {
+        mbar_arrive_expect_tx(&bars[slot], 2u * copy_bytes);
+        bulk_load(ring + size_t(slot) * SLOT_BYTES, plan + int64_t(ra) * ldp, 2u * copy_bytes,
+                  &bars[slot], policy);
+      } else if (copy_bytes) {
         mbar_arrive_expect_tx(&bars[slot], copy_bytes * (rb >= 0 ? 2u : 1u));
         bulk_load(ring + size_t(slot) * SLOT_BYTES, plan + int64_t(ra) * ldp + col0, copy_bytes,
                   &bars[slot], policy);
         if (rb >= 0)
-          bulk_load(ring + size_t(slot) * SLOT_BYTES + ROW_BYTES, plan + int64_t(rb) * ldp + col0,
+          bulk_load(ring + size_t(slot) * SLOT_BYTES + rowb_off, plan + int64_t(rb) * ldp + col0,
                     copy_bytes, &bars[slot], policy);
       } else {
         mbar_arrive(&bars[slot]);
@@ -219,7 +232,7 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
       xa[k] = load_raw(sbase, ra, k);
-      xb[k] = lb ? load_raw(sbase + ROW_BYTES, rb, k) : make_uint4(0u, 0u, 0u, 0u);
+      xb[k] = lb ? load_raw(sbase + rowb_off, rb, k) : make_uint4(0u, 0u, 0u, 0u);
     }
     float sa = 0.0f, sb = 0.0f;
 #pragma unroll
@@ -314,7 +327,7 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
         E::unpack(xb[k], fb);
       } else {
         E::unpack(load_raw(sbase, ra, k), fa);
-        E::unpack(lb ? load_raw(sbase + ROW_BYTES, rb, k) : make_uint4(0u, 0u, 0u, 0u), fb);
+        E::unpack(lb ? load_raw(sbase + rowb_off, rb, k) : make_uint4(0u, 0u, 0u, 0u), fb);
       }
 #pragma unroll
       for (int e = 0; e < VE; ++e) cacc[k][e] = fmaf(ub, fb[e], fmaf(ua, fa[e], cacc[k][e]));
