@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import convex
 from paper_2412_11079_gb300 import workloads
 
 torch = pytest.importorskip("torch")
@@ -75,6 +76,35 @@ def test_fp32_kernel_form_matches_oracle(uot, n, m):
     np.testing.assert_allclose(V, Vr / g, rtol=FP32_TOL)
     c_ref = oracle.transport_cost(ref.plan, p.C)
     assert abs(cost - c_ref) <= FP32_TOL * abs(c_ref)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, FP32_TOL), (torch.bfloat16, LOW_TOL)])
+def test_balanced_kernel_form(uot, dtype, tol):
+    """reg_m = inf (fi = 1): balanced Sinkhorn, the special case the paper's
+    introduction names for the same interleaving.  The kernel form follows the
+    oracle, and the plan's column sums equal b after the last iteration in
+    either storage precision (V is formed from the stored K's own sums)."""
+    p = workloads.uniform2d(seed=21, n=700, m=1500, reg=0.1, reg_m=math.inf, iters=30)
+    plan, cost, U, V, res = kform_gpu(uot, p, dtype=dtype)
+    ref = oracle.sinkhorn(oracle.init_plan(p.C, p.reg), p.a, p.b, p.reg, math.inf, p.iters)
+    assert res.dev_status == 0 and res.iters_done == p.iters
+    assert rel_err(plan, ref.plan) <= tol
+    np.testing.assert_allclose(plan.sum(axis=0), p.b, rtol=2e-5)
+
+
+def test_balanced_limit_is_entropic_ot(uot):
+    """fi = 1 and equal masses: the kernel form's limit is the entropic OT
+    plan, here from Newton's method on the dual (no Sinkhorn step shared)."""
+    p = workloads.uniform2d(seed=22, n=40, m=30, reg=0.1, reg_m=math.inf, iters=300)
+    p.b = (p.b.astype(np.float64) * (p.a.astype(np.float64).sum()
+                                     / p.b.astype(np.float64).sum())).astype(np.float32)
+    plan, cost, U, V, res = kform_gpu(uot, p)
+    a = p.a.astype(np.float64)
+    b = p.b.astype(np.float64)
+    b *= a.sum() / b.sum()
+    ref = convex.entropic_ot_newton(p.C.astype(np.float64), a, b, p.reg)
+    assert res.dev_status == 0
+    assert rel_err(plan, ref) <= FP32_TOL
 
 
 def test_kernel_form_misaligned_ld_and_scale(uot):
