@@ -20,6 +20,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-5
+RUN_TOL_500 = 4e-5  # two GPU runs of 500 FP32 iterations (see test_large_case_full_size)
 
 
 @pytest.fixture(scope="module")
@@ -308,7 +309,13 @@ def test_large_case_full_size(uot):
     assert torch.isfinite(plan).all().item()
     d = ((plan.double() - last.double()).abs() /
          torch.clamp(last.double().abs(), min=1e-6 * last.abs().max().item())).max().item()
-    assert d <= FP32_TOL
+    # Two GPU runs add each column's partial sums in different orders (the
+    # dynamic row schedule and the atomic folding vary between runs): a
+    # relative difference of about fi * u * sqrt(rows per CTA) ~ 5e-7 in a
+    # column factor per iteration (u = 2^-24, ~108 rows per CTA), a random
+    # walk of ~1.1e-5 over 500 iterations.  Carried state other than the plan
+    # would differ at order 1e-1.
+    assert d <= RUN_TOL_500
     S = state.double().cpu().numpy()
     one = oracle.sinkhorn(S, p.a, p.b, p.reg, p.reg_m, 1).plan
     assert rel_err(last.double().cpu().numpy(), one) <= FP32_TOL
