@@ -376,6 +376,9 @@ def run_grad(args):
     # overlaps with the other problems' passes.
     branches = [torch.cuda.Stream() for _ in range(min(args.grad_streams, len(bufs)))]
     opt = uot.options(max_ctas=args.grad_max_ctas)
+    # The adjoint's launches are limited separately: a reverse step (12 bytes
+    # per element, one row per step) overlapped best in narrower launches.
+    bopt = uot.options(max_ctas=args.grad_bwd_max_ctas)
 
     def step(s):
         for br in branches:
@@ -386,7 +389,7 @@ def run_grad(args):
             uot.uot_sinkhorn_kform_save(K, a, b, p.reg, p.reg_m, iters, U, V, hist, ws, bs, opt)
             uot.uot_kform_cost(K, U, V, C, cost, bs)
             uot.uot_sinkhorn_backward(K, C, a, b, p.reg, p.reg_m, iters, hist, 1.0, dC, da, db,
-                                      bws, bs, opt)
+                                      bws, bs, bopt)
         for br in branches:
             s.wait_stream(br)
 
@@ -443,6 +446,7 @@ def run_grad(args):
         "unit": UNIT, "ms_per_step": ms, "elems_per_s": elems / (ms * 1e-3),
         "forward_ms": fwd_ms, "backward_ms": ms - fwd_ms,
         "branches": len(branches), "max_ctas_per_launch": args.grad_max_ctas,
+        "max_ctas_per_adjoint_launch": args.grad_bwd_max_ctas,
         "alg_gbs": (elems * (4.0 + 12.0)) / (ms * 1e-3) / 1e9,
         "grad_rel_err": {"iters": q.iters, "dC": rel(Cq.grad, rdC), "da": rel(aq.grad, rda),
                          "db": rel(bq.grad, rdb)},
@@ -479,8 +483,9 @@ def main():
                     help="batched workload: fixed schedule stages,max_team,target,cluster "
                          "(skips the autotuner)")
     ap.add_argument("--grad-check-iters", type=int, default=5)
-    ap.add_argument("--grad-streams", type=int, default=8)
+    ap.add_argument("--grad-streams", type=int, default=16)
     ap.add_argument("--grad-max-ctas", type=int, default=80)
+    ap.add_argument("--grad-bwd-max-ctas", type=int, default=40)
     ap.add_argument("--acc-n", type=int, default=8192)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
