@@ -189,8 +189,8 @@ uot_status uot_init_kernel_scaled(const float* C, int64_t ldc, void* K, int64_t 
  * P_ij = U_i K_ij V_j for K as stored.  U and V are determined up to a common
  * power of two (U 2^e, V 2^-e): at the fixed point the row factors tend to
  * k = (sum a / sum b)^(fi/(2-fi)) and the column factors to 1/k, so each pass
- * moves an exact power of two between them to keep both in FP32 range.  U and V are overwritten (the call
- * starts from U = 2^-k_log2_scale, V = 1).  Row/column sums, factors and
+ * moves an exact power of two between them to keep both in FP32 range.  U
+ * and V are overwritten (the call starts from U = 2^-k_log2_scale, V = 1).  Row/column sums, factors and
  * scalings are FP32; the stopping error is FP64 (same rule as uot_sinkhorn).
  * Only the fused algorithm exists in this form.  Other arguments, the
  * workspace and errors are those of uot_sinkhorn.
@@ -321,9 +321,12 @@ uot_status uot_sinkhorn_noalloc(void* plan, int64_t ldp, const float* a, const f
  *              distributed shared memory for the column sums);
  *   streaming  the others are grouped into size classes served by teams of
  *              CTAs (a power of two, more CTAs for larger problems) in one
- *              persistent cooperative launch; inside a team, rows are shared
- *              dynamically and the team meets at a bounded software barrier
- *              once per iteration.
+ *              persistent cooperative launch; inside a team each CTA owns a
+ *              contiguous block of rows for all iterations (its row
+ *              scalings stay in shared memory), and the team meets at a
+ *              bounded software barrier once per iteration.  Both engines
+ *              keep the plan in kernel form during the iterations (K read,
+ *              FP32 scalings updated) and write diag(U) K diag(V) at the end.
  */
 typedef struct uot_problem {
   void* plan;        /* device, n x m FP32, row-major; 16-byte aligned, ldp % 4 == 0 */
