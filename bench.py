@@ -8,10 +8,17 @@ whole solve: P0 = exp(-C/reg), 500 fused iteration passes plus the finishing
 sweep, and the FP64 transport cost.  ``value`` counts plan elements processed
 per second (N*M*iters per step) with C, a, b already resident on the GPU;
 ``e2e`` repeats the same solve through the public API from pinned host
-buffers (C, a, b copied in, plan and cost copied out inside the timed region).
+buffers (C, a, b copied in, plan and cost copied out inside the timed region;
+steps double-buffered so one step's copies overlap its neighbours' solves).
 
 ``--impl reference`` times the FP64 CPU oracle on the same workload instead
 (each step is a bounded sample: one oracle iteration on the full-size plan).
+
+Other workloads print one JSON line of their own: ``--workload precision``
+(N=M=32768, every storage form, accuracy at 8192^2 against the oracle),
+``--workload batched`` (512 uneven problems in one set of launches against a
+loop of single-problem launches) and ``--workload grad`` (32 problems of
+2048^2, forward and adjoint in one CUDA graph).
 
 Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 run it
 under ``torch.distributed.run`` -- every rank then solves its own problem
