@@ -4,7 +4,8 @@ autotuner for the one-launch batched iteration (uot_sinkhorn_batched).
 Plans are stored with a leading dimension rounded up to a multiple of 4 so
 every row starts on a 16-byte boundary (the bulk copies need it).  The
 autotuner times candidate schedules (ring depth, largest team, target work
-per CTA) on the batch itself and keeps the fastest, cached per batch shape.
+per CTA, largest on-chip cluster) on the batch itself and keeps the fastest,
+cached per batch shape.
 """
 
 from __future__ import annotations

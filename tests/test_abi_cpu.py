@@ -144,3 +144,20 @@ def test_product_path_never_imports_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f
                 assert "oracle/" not in text, f
+
+
+def test_batch_autotuner_candidates_keep_the_tuning_contract(lib):
+    """Every schedule the autotuner may pick is one include/uot.h accepts:
+    ring depth 2..6, a power-of-two team, positive work per CTA, an on-chip
+    cluster cap of 0, 1, 2, 4, 8 or 16, reserved fields zero; defaults too."""
+    pytest.importorskip("torch")
+    from paper_2412_11079_gb300 import batch, uot
+    cands = batch.candidates()
+    assert len(cands) == len({(t.stages, t.max_team, t.target_elems, t.resident_max_cluster)
+                              for t in cands})
+    for t in cands + [uot.batch_tuning()]:
+        assert 2 <= t.stages <= 6
+        assert t.max_team >= 1 and t.max_team & (t.max_team - 1) == 0
+        assert t.target_elems > 0
+        assert t.resident_max_cluster in (0, 1, 2, 4, 8, 16)
+        assert list(t.reserved) == [0, 0, 0]
