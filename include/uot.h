@@ -118,6 +118,21 @@ size_t uot_workspace_size(int64_t n, int64_t m, const uot_options* opt);
 uint64_t uot_launch_count(void);
 
 /*
+ * uot_selftest_wait -- shows on the device that the library's bounded waits
+ * give up instead of hanging (failure detection without a GPU fault).  One
+ * thread waits on an mbarrier phase with the same helper the bulk-copy rings
+ * use, then spins with acquire loads on the device int *counter_dev until it
+ * reaches `target`, as the inter-CTA barriers do; each wait gives up after
+ * limit_s seconds (0 < limit_s <= 10).  With complete == 0 nothing arrives
+ * on the barrier.  status_dev (two device uint32) receives UOT_DEV_TIMEOUT
+ * or 0 for the barrier and for the counter.  The kernel returns either way
+ * and the context stays usable.  Asynchronous.  Errors: UOT_ERR_INVALID_ARG
+ * (NULL or misaligned pointers, limit out of range), UOT_ERR_CUDA.
+ */
+uot_status uot_selftest_wait(const int32_t* counter_dev, int32_t target, int32_t complete,
+                             double limit_s, uint32_t* status_dev, void* stream);
+
+/*
  * uot_init_kernel -- initial plan P0_ij = exp(-C_ij / reg).
  * Section 2.1 starts from a "given matrix"; the Gibbs kernel of the cost is
  * the usual one for entropic transport.  C: n x m FP32, leading dimension ldc.

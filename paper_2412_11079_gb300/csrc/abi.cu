@@ -80,6 +80,19 @@ size_t uot_workspace_size(int64_t n, int64_t m, const uot_options* opt) {
 
 uint64_t uot_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+uot_status uot_selftest_wait(const int32_t* counter_dev, int32_t target, int32_t complete,
+                             double limit_s, uint32_t* status_dev, void* stream) {
+  if (!counter_dev || !status_dev || !(limit_s > 0.0) || !(limit_s <= 10.0))
+    return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(counter_dev) % 4 || reinterpret_cast<uintptr_t>(status_dev) % 4)
+    return UOT_ERR_INVALID_ARG;
+  const uint64_t limit_ns = uint64_t(limit_s * 1e9);
+  cudaError_t e = launch_wait_selftest(counter_dev, target, complete ? 1 : 0, limit_ns, status_dev,
+                                       static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) count_launch();
+  return e == cudaSuccess ? UOT_OK : UOT_ERR_CUDA;
+}
+
 uot_status uot_init_kernel(const float* C, int64_t ldc, void* plan, int64_t ldp, int64_t n,
                            int64_t m, float reg, const uot_options* opt, void* stream) {
   const uot_options o = resolve(opt);

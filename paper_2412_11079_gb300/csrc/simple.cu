@@ -407,6 +407,40 @@ cudaError_t launch_cost(const void* P, int64_t ldp, const float* C, int64_t ldc,
   });
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier phase with
+// the helper every bulk-copy ring uses (mbar_wait_bounded), then spins on a
+// global counter with an acquire load until it reaches `target`, the pattern
+// of the inter-CTA barriers, each wait giving up after limit_ns.  Unless
+// `complete` is set nothing arrives on the barrier.  Each outcome goes to
+// status[0] (barrier) and status[1] (counter): DEV_TIMEOUT or 0.
+__global__ void wait_selftest_kernel(const int* counter, int target, int complete,
+                                     uint64_t limit_ns, uint32_t* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  if (complete) mbar_arrive(&bar);
+  status[0] = mbar_wait_bounded(&bar, 0u, limit_ns) ? 0u : DEV_TIMEOUT;
+  uint32_t st = 0;
+  const uint64_t t0 = global_timer_ns();
+  while (ld_acquire_gpu(counter) < target) {
+    if (global_timer_ns() - t0 > limit_ns) {
+      st = DEV_TIMEOUT;
+      break;
+    }
+  }
+  status[1] = st;
+}
+
+cudaError_t launch_wait_selftest(const int* counter, int target, int complete, uint64_t limit_ns,
+                                 uint32_t* status, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(counter, target, complete, limit_ns, status);
+  return last();
+}
+
 cudaError_t launch_reset(uint8_t* ws, WsLayout L, const float* b, int m, cudaStream_t s) {
   const int blocks = int((L.mpad + TB - 1) / TB);
   reset_kernel<<<blocks, TB, 0, s>>>(reinterpret_cast<Control*>(ws + L.ctl),

@@ -73,6 +73,7 @@ SIGNATURES = {
     "uot_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "uot_workspace_size": (_SZ, [_I64, _I64, ctypes.POINTER(UotOptions)]),
     "uot_launch_count": (ctypes.c_uint64, []),
+    "uot_selftest_wait": (ctypes.c_int, [_P, _I32, _I32, _D, _P, _P]),
     "uot_init_kernel": (ctypes.c_int, [_P, _I64, _P, _I64, _I64, _I64, _F,
                                        ctypes.POINTER(UotOptions), _P]),
     "uot_sinkhorn": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _D, _P, _SZ,
@@ -192,6 +193,18 @@ def uot_workspace_size(n: int, m: int, opt: UotOptions | None = None) -> int:
 
 def uot_launch_count() -> int:
     return int(load().uot_launch_count())
+
+
+def uot_selftest_wait(counter, target: int, complete: bool, limit_s: float, status, stream=None):
+    """Runs the bounded-wait self-test: `counter` a one-element int32 device
+    tensor, `status` a two-element int32 device tensor receiving
+    UOT_DEV_TIMEOUT or 0 for the barrier and the counter wait.  Async."""
+    torch = _torch()
+    if counter.dtype != torch.int32 or status.dtype != torch.int32 or status.numel() < 2:
+        raise ValueError("counter and status must be int32 device tensors (status of 2)")
+    _check(load().uot_selftest_wait(counter.data_ptr(), int(target), 1 if complete else 0,
+                                    float(limit_s), status.data_ptr(), _stream(stream)),
+           "uot_selftest_wait")
 
 
 def uot_fused_config(k: int):

@@ -161,3 +161,14 @@ def test_batch_autotuner_candidates_keep_the_tuning_contract(lib):
         assert t.target_elems > 0
         assert t.resident_max_cluster in (0, 1, 2, 4, 8, 16)
         assert list(t.reserved) == [0, 0, 0]
+
+
+def test_wait_selftest_validates_arguments_without_a_gpu(lib):
+    from paper_2412_11079_gb300 import uot
+    P = ctypes.c_void_p(4096)  # never dereferenced: validation fails first
+    f = lib.uot_selftest_wait
+    assert f(None, 1, 0, 0.1, P, None) == uot.UOT_ERR_INVALID_ARG
+    assert f(P, 1, 0, 0.1, None, None) == uot.UOT_ERR_INVALID_ARG
+    for bad in (0.0, -1.0, 11.0, math.nan):
+        assert f(P, 1, 0, bad, P, None) == uot.UOT_ERR_INVALID_ARG
+    assert f(ctypes.c_void_p(4098), 1, 0, 0.1, P, None) == uot.UOT_ERR_INVALID_ARG
