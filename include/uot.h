@@ -15,6 +15,8 @@
  *  - Matrices are dense and row-major with a leading dimension (elements
  *    between row starts) >= the number of columns.  All array pointers are
  *    DEVICE pointers owned by the caller unless stated otherwise.
+ *  - Sizes: 1 <= n, m <= 2^30 (row and column indices and the per-pass row
+ *    counters stay in 32-bit range); other sizes are UOT_ERR_INVALID_ARG.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Work is enqueued asynchronously; nothing synchronises unless stated.
  *  - Nothing is allocated or freed on the device by the library; scratch

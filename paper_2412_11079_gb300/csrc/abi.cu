@@ -19,8 +19,10 @@ static size_t esize(int dtype) { return dtype == UOT_F32 ? 4 : 2; }
 
 static bool valid_dtype(int d) { return d == UOT_F32 || d == UOT_BF16 || d == UOT_F16; }
 
+// Row and column indices and the per-pass row counters (which may run a few
+// ring depths per CTA past n) are 32-bit in the kernels.
 static bool valid_dims(int64_t n, int64_t m) {
-  return n >= 1 && m >= 1 && n <= INT32_MAX && m <= INT32_MAX / 2;
+  return n >= 1 && m >= 1 && n <= (int64_t(1) << 30) && m <= (int64_t(1) << 30);
 }
 
 static uot_options resolve(const uot_options* opt) {

@@ -172,3 +172,11 @@ def test_wait_selftest_validates_arguments_without_a_gpu(lib):
     for bad in (0.0, -1.0, 11.0, math.nan):
         assert f(P, 1, 0, bad, P, None) == uot.UOT_ERR_INVALID_ARG
     assert f(ctypes.c_void_p(4098), 1, 0, 0.1, P, None) == uot.UOT_ERR_INVALID_ARG
+
+
+def test_size_limits(lib):
+    """1 <= n, m <= 2^30: the kernels' indices and row counters stay 32-bit."""
+    assert lib.uot_workspace_size(1 << 30, 4, None) > 0
+    assert lib.uot_workspace_size(4, 1 << 30, None) > 0
+    for n, m in ((0, 4), (4, 0), ((1 << 30) + 1, 4), (4, (1 << 30) + 1), (-1, 4)):
+        assert lib.uot_workspace_size(n, m, None) == 0
