@@ -307,9 +307,12 @@ uot_status uot_cost(const void* plan, int64_t ldp, const float* C, int64_t ldc,
  *  - Size limit: problems whose uot_workspace_size(n, m, opt) exceeds
  *    UOT_STATIC_SCRATCH_BYTES (2 MiB) are rejected with UOT_ERR_WORKSPACE
  *    before anything is enqueued; N = M = 32768 needs about 1 MiB.
- *  - Set-up: the first call on a device (with that device current) looks up
- *    the array's device address once; make that first call before any stream
- *    capture on that device.
+ *  - Set-up: the array's device address belongs to the CUDA context that
+ *    loaded the library's module, so the first call in each context -- on
+ *    each device, again after cudaDeviceReset, and in any context the caller
+ *    creates and makes current -- looks it up once (keyed by the driver's
+ *    context id) with that context current; make that first call before any
+ *    stream capture in that context.
  *  - Sharing: every call on a device uses the same array, and the array keeps
  *    the last call's contents (each call re-initialises what must start at
  *    zero).  Calls whose work overlaps on the GPU -- on different streams, or

@@ -73,3 +73,38 @@ def test_noalloc_rejects_problems_beyond_the_static_scratch(uot):
     st = uot.load().uot_sinkhorn_noalloc(plan.data_ptr(), big, a.data_ptr(), b.data_ptr(),
                                          big, big, 0.1, 1.0, 1, 0.0, None, None, None)
     assert st == uot.UOT_ERR_WORKSPACE
+
+
+def test_noalloc_from_a_new_host_thread(uot):
+    """A host thread that has made no CUDA call has no current context; the
+    first call there still finds the array's address (the runtime makes the
+    device's primary context current) and matches uot_sinkhorn.  Every tensor
+    is made on the main thread, so the worker's only CUDA call is the entry
+    point itself (on the legacy default stream)."""
+    import threading
+
+    p = workloads.uniform2d(seed=33, n=200, m=300, reg=0.1, reg_m=1.0, iters=12)
+    n, m = p.C.shape
+    C = torch.from_numpy(p.C).cuda()
+    a = torch.from_numpy(p.a).cuda()
+    b = torch.from_numpy(p.b).cuda()
+    p0 = torch.empty((n, m), device="cuda")
+    uot.uot_init_kernel(C, p0, p.reg)
+    ref_plan, got_plan = p0.clone(), p0.clone()
+    ref = uot.uot_sinkhorn(ref_plan, a, b, p.reg, p.reg_m, p.iters)
+    torch.cuda.synchronize()
+    res = uot.UotResult()
+    out = {}
+
+    def worker():
+        out["st"] = uot.load().uot_sinkhorn_noalloc(
+            got_plan.data_ptr(), m, a.data_ptr(), b.data_ptr(), n, m, p.reg, p.reg_m, p.iters,
+            0.0, None, None, ctypes.byref(res))
+
+    t = threading.Thread(target=worker)
+    t.start()
+    t.join()
+    torch.cuda.synchronize()
+    assert out["st"] == uot.UOT_OK, uot.uot_status_string(out["st"])
+    assert res.dev_status == ref.dev_status == 0 and res.iters_done == p.iters
+    assert rel_err(got_plan.double().cpu().numpy(), ref_plan.double().cpu().numpy()) <= FP32_TOL
