@@ -76,6 +76,24 @@ typedef enum uot_algo { UOT_ALGO_FUSED = 0, UOT_ALGO_MULTIPASS = 1 } uot_algo;
  *        fi = 1.  The adjoint (uot_sinkhorn_backward) is for PAPER only. */
 typedef enum uot_rule { UOT_RULE_PAPER = 0, UOT_RULE_POT = 1 } uot_rule;
 
+/* How uot_sinkhorn keeps the plan during the iterations (both give the plan
+ * after the column step of the last iteration in `plan` on return).
+ * INPLACE: every fused pass reads the plan and writes it back rescaled, one
+ *          read and one write per iteration (Section 3.1's minimum for a
+ *          rewritten plan).  Each pass rounds every entry (twice), and near
+ *          the fixed point the factors change little from pass to pass, so
+ *          an entry can be rounded the same way many times: in FP32 the
+ *          worst entry's error grows about linearly with the iteration count
+ *          (measured on the GPU against the FP64 rule: 2.6e-6 after 100,
+ *          8e-6 after 500 iterations of a 2048 x 16384 plan).
+ * KFORM:   the plan of Section 2.1 is always diag(U) K diag(V) with K the
+ *          initial plan, so the buffer is kept as K, read-only, while FP32
+ *          scalings U (in the workspace) and V are updated; one read per
+ *          iteration, and a last sweep writes U_i K_ij V_j over the buffer.
+ *          Every entry is rounded once at the end (1.1e-6 after 500
+ *          iterations of the same plan).  Fused algorithm only. */
+typedef enum uot_storage { UOT_STORAGE_INPLACE = 0, UOT_STORAGE_KFORM = 1 } uot_storage;
+
 /* Bits of uot_result.dev_status. */
 #define UOT_DEV_ZERO_SUM 1u
 #define UOT_DEV_NONFINITE 2u
@@ -92,6 +110,16 @@ typedef struct uot_options {
                            launch (to run several solves side by side, e.g.
                            as parallel branches of one CUDA graph)          */
   int32_t rule;         /* uot_rule (default UOT_RULE_PAPER)                  */
+  int32_t storage;      /* uot_storage of uot_sinkhorn (default INPLACE)      */
+  int32_t deterministic;/* 1: bit-identical results from run to run with the
+                           same inputs, options and device: every CTA keeps a
+                           fixed set of rows, writes its column partial sums
+                           to its own slot of the workspace, and a reduction
+                           launch after each pass adds the slots in a fixed
+                           order (instead of floating-point atomics and a
+                           dynamic row schedule).  Slower (static rows, one
+                           more launch per iteration); one row per step.
+                           uot_sinkhorn and uot_sinkhorn_kform only.        */
   int32_t reserved[1];  /* must be 0                                          */
   void* pass_events[2]; /* optional cudaEvent_t pair: uot_sinkhorn records
                            [0] on `stream` just before its first iteration

@@ -75,9 +75,8 @@ const char* uot_status_string(uot_status s) {
 }
 
 size_t uot_workspace_size(int64_t n, int64_t m, const uot_options* opt) {
-  (void)opt;
   if (!valid_dims(n, m)) return 0;
-  return ws_layout(n, m).total;
+  return ws_layout(n, m, opt && opt->deterministic != 0).total;
 }
 
 uint64_t uot_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
@@ -145,11 +144,20 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
     return UOT_ERR_INVALID_ARG;
   if (std::isnan(tol) || std::isinf(tol) || !reserved_zero(o)) return UOT_ERR_INVALID_ARG;
   if (o.rule != UOT_RULE_PAPER && o.rule != UOT_RULE_POT) return UOT_ERR_INVALID_ARG;
+  if (o.storage != UOT_STORAGE_INPLACE && o.storage != UOT_STORAGE_KFORM) return UOT_ERR_INVALID_ARG;
+  if (o.deterministic != 0 && o.deterministic != 1) return UOT_ERR_INVALID_ARG;
+  if (o.algo != UOT_ALGO_FUSED && o.algo != UOT_ALGO_MULTIPASS) return UOT_ERR_INVALID_ARG;
+  const bool det = o.deterministic == 1;
+  // uot_sinkhorn with kernel-form storage: the plan buffer is K (read-only
+  // during the iterations), U lives in the workspace, V in the factor buffer,
+  // and a last sweep writes U_i K_ij V_j over the buffer.
+  const bool kstore = !kf && o.storage == UOT_STORAGE_KFORM;
+  const bool kfo = kf || kstore;  // the iterations run in kernel form
+  if ((kstore || det) && o.algo != UOT_ALGO_FUSED) return UOT_ERR_UNSUPPORTED;
   // The scaling-vector rule needs the scalings (kernel form); the adjoint's
   // history is for the rule of Section 2.1.
-  if (o.rule == UOT_RULE_POT && (!kf || hist)) return UOT_ERR_UNSUPPORTED;
+  if (o.rule == UOT_RULE_POT && (!kfo || hist)) return UOT_ERR_UNSUPPORTED;
   const bool pot = o.rule == UOT_RULE_POT;
-  if (o.algo != UOT_ALGO_FUSED && o.algo != UOT_ALGO_MULTIPASS) return UOT_ERR_INVALID_ARG;
   if (o.cluster < 0 || o.cluster > 8 || o.tile < 0 || o.max_ctas < 0) return UOT_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(mat) % esize(o.dtype) ||
       reinterpret_cast<uintptr_t>(a) % 4 || reinterpret_cast<uintptr_t>(b) % 4)
@@ -158,7 +166,7 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
              !std::isfinite(k_log2_scale) || std::fabs(k_log2_scale) > 100.0f ||
              k_log2_scale != std::nearbyint(k_log2_scale) || o.algo != UOT_ALGO_FUSED))
     return UOT_ERR_INVALID_ARG;
-  const WsLayout L = ws_layout(n, m);
+  const WsLayout L = ws_layout(n, m, det);
   if (!workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(workspace) % 256)
     return UOT_ERR_WORKSPACE;
   const HistLayout HL = hist_layout(n, m, iters);
@@ -180,8 +188,9 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
   const bool tma_ok = reinterpret_cast<uintptr_t>(mat) % 16 == 0 &&
                       (uint64_t(ldm) * esize(o.dtype)) % 16 == 0;
   // Kernel form with bulk copies and no forced configuration: two rows per
-  // step (kform_pair.cu).
-  if (kf && o.algo == UOT_ALGO_FUSED && iters > 0 && tma_ok && o.tile == 0 && o.cluster == 0)
+  // step (kform_pair.cu); deterministic mode keeps the one-row pass.
+  if (kfo && o.algo == UOT_ALGO_FUSED && iters > 0 && tma_ok && o.tile == 0 && o.cluster == 0 &&
+      !det)
     pair = kform_pair_pick(o.dtype, m, &cs);
   if (pair >= 0) {
     if (kform_pair_geometry(pair, cs, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
@@ -194,12 +203,15 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
     cs = o.cluster > 0 ? o.cluster : int((m + cfg.cols - 1) / cfg.cols);
     if (cs > 8) return UOT_ERR_UNSUPPORTED;
     if (int64_t(cs) * cfg.cols < m) return UOT_ERR_INVALID_ARG;
-    if (fused_geometry(kf, k, cs, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
+    if (fused_geometry(kfo, k, cs, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
     if (o.max_ctas > 0 && grid > o.max_ctas) grid = std::max(cs, (o.max_ctas / cs) * cs);
+    // Deterministic mode: one slot of column partials per row group.
+    if (det && grid > DET_SLOTS * cs) grid = DET_SLOTS * cs;
   }
 
+  if (kstore) U = reinterpret_cast<float*>(ws + L.u);
   if (launch_reset(ws, L, b, M, s) != cudaSuccess) return UOT_ERR_CUDA;
-  if (kf && launch_kform_reset(U, N, std::ldexp(1.0f, -int(std::lround(k_log2_scale))),
+  if (kfo && launch_kform_reset(U, N, std::ldexp(1.0f, -int(std::lround(k_log2_scale))),
                                reinterpret_cast<float*>(ws + L.beta), M, int(L.mpad), a, b, fi,
                                pot, reinterpret_cast<double*>(ws + L.log2k), s) != cudaSuccess)
     return UOT_ERR_CUDA;
@@ -239,7 +251,10 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
     A.ctl = reinterpret_cast<Control*>(ws + L.ctl);
     A.stages = stages;
     A.b_ws = reinterpret_cast<const float*>(ws + L.bws);
-    A.dynamic = 1;
+    A.dynamic = det ? 0 : 1;
+    A.det = det ? 1 : 0;
+    A.part = reinterpret_cast<float*>(ws + L.part);
+    A.err_part = reinterpret_cast<double*>(ws + L.err_part);
     A.U = U;
     A.log2k = reinterpret_cast<const double*>(ws + L.log2k);
     A.beta = reinterpret_cast<const float*>(ws + L.beta);
@@ -255,7 +270,7 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
     }
     for (int t = 1; t <= iters; ++t) {
       A.t = t;
-      A.first = !kf && t == 1;  // the kernel form starts from V = 1 in the buffer
+      A.first = !kfo && t == 1;  // the kernel form starts from V = 1 in the buffer
       A.check_prev = track && (t - 1) >= 2 && ((t - 1) % o.check_every) == 0;
       A.c_prev = c[(t - 1) % 3];
       A.c_next = c[t % 3];
@@ -276,13 +291,21 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
         A.save_V = reinterpret_cast<float*>(hb + HL.V + size_t(t) * HL.strideV);
       }
       const cudaError_t le = pair >= 0 ? kform_pair_launch(pair, cs, grid, smem, A, s)
-                                       : fused_launch(kf, k, cs, grid, smem, tma, A, s);
+                                       : fused_launch(kfo, k, cs, grid, smem, tma, A, s);
       if (le != cudaSuccess) return UOT_ERR_CUDA;
+      if (det && det_reduce_launch(kfo, grid / cs, A, s) != cudaSuccess) return UOT_ERR_CUDA;
     }
     if (ev1 && cudaEventRecord(ev1, s) != cudaSuccess) return UOT_ERR_CUDA;
-    const cudaError_t e =
-        kf ? launch_kform_finish(V, M, iters, ws, L, tol, s)
-           : launch_finish(mat, ldm, N, M, o.dtype, b, fi, iters, ws, L, tol, o.check_every, true, s);
+    float* Vws = reinterpret_cast<float*>(ws + L.beta);
+    cudaError_t e;
+    if (kf) {
+      e = launch_kform_finish(V, M, iters, ws, L, tol, s);
+    } else if (kstore) {
+      e = launch_kform_finish(Vws, M, iters, ws, L, tol, s);
+      if (e == cudaSuccess) e = launch_kform_materialize(mat, ldm, o.dtype, U, Vws, N, M, s);
+    } else {
+      e = launch_finish(mat, ldm, N, M, o.dtype, b, fi, iters, ws, L, tol, o.check_every, true, s);
+    }
     if (e != cudaSuccess) return UOT_ERR_CUDA;
   }
   if (!out) return UOT_OK;

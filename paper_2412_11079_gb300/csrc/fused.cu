@@ -169,6 +169,70 @@ cudaError_t fused_geometry(bool kf, int k, int cs, int n, int* grid, int* stages
   return cudaSuccess;
 }
 
+// Deterministic mode, after a pass: column j's sum of iteration t is the
+// slots' partials added in slot order (each of the 8 warps of a CTA adds
+// every 8th slot for 32 columns, then one warp adds the 8 results in warp
+// order), so it does not depend on which CTA finished first.  The next
+// factors follow as in the end-of-pass job of the pass kernel.  A pass that
+// found the stopping rule already met leaves everything as it is.
+constexpr int DR_WARPS = 8;
+
+template <bool KF>
+__global__ void __launch_bounds__(DR_WARPS * 32) det_reduce_kernel(const FusedArgs p,
+                                                                   int groups) {
+  __shared__ float part[DR_WARPS][32];
+  if (p.track && *reinterpret_cast<volatile int32_t*>(&p.ctl->done)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  float s = 0.0f;
+  if (j < p.m)
+    for (int g = warp; g < groups; g += DR_WARPS) s += __ldcg(p.part + size_t(g) * p.mpad + j);
+  part[warp][lane] = s;
+  __syncthreads();
+  uint32_t st = 0;
+  if (warp == 0 && j < p.m) {
+    float c = 0.0f;
+#pragma unroll
+    for (int w = 0; w < DR_WARPS; ++w) c += part[w][lane];
+    p.c_next[j] = c;
+    if constexpr (KF) {
+      const float inv_gauge = ldexpf(1.0f, -gauge_exponent(p.t, float(*p.log2k)));
+      const float v = p.beta_out[j];
+      const float cc = v * c * inv_gauge;
+      const float v_new = p.pot ? rescale_factor(p.b_ws[j], c, p.fi, st)
+                                : v * rescale_factor(p.b_ws[j], cc, p.fi, st) * inv_gauge;
+      p.beta_out[j] = v_new;
+      if (p.save_c) {
+        p.save_c[j] = cc;
+        p.save_V[j] = v_new;
+      }
+    } else {
+      p.beta_out[j] = rescale_factor(p.b_ws[j], c, p.fi, st);
+    }
+  }
+  if (p.track && blockIdx.x == 0 && threadIdx.x == 0) {
+    double num = 0.0, den = 0.0;
+    for (int g = 0; g < groups; ++g) {
+      num += p.err_part[2 * g];
+      den += p.err_part[2 * g + 1];
+    }
+    p.err_next[0] = num;
+    p.err_next[1] = den;
+  }
+  if (st) atomicOr(&p.ctl->status, st);
+}
+
+cudaError_t det_reduce_launch(bool kf, int groups, const FusedArgs& args, cudaStream_t s) {
+  const int blocks = (args.m + 31) / 32;
+  if (kf)
+    det_reduce_kernel<true><<<blocks, DR_WARPS * 32, 0, s>>>(args, groups);
+  else
+    det_reduce_kernel<false><<<blocks, DR_WARPS * 32, 0, s>>>(args, groups);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
 cudaError_t fused_launch(bool kf, int k, int cs, int grid, size_t smem, bool tma,
                          const FusedArgs& args, cudaStream_t s) {
   const FusedEntry& e = table(kf)[k];

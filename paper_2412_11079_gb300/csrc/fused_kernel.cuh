@@ -41,6 +41,10 @@
 //
 // Column partial sums are combined with floating-point atomics, so their
 // order (and the last bits of the column sums) can differ from run to run.
+// Deterministic mode (p.det) keeps the static schedule for every row width,
+// stores each row group's partials to a slot of its own instead, and leaves
+// the next factors to a reduction launch that adds the slots in slot order
+// (det_reduce_kernel): the same inputs then give the same bits.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -397,8 +401,31 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
     ++done_rows;
   }
 
-  // Fold this CTA's column partials into the column sums of iteration t.
-  if (done_rows > 0) {
+  // Fold this CTA's column partials into the column sums of iteration t:
+  // with vector reductions, or, in deterministic mode, by storing them (zeros
+  // included) to this row group's slot, which a reduction launch adds to the
+  // other slots in slot order.
+  if (p.det) {
+    float* slot = p.part + size_t(cid) * size_t(p.mpad);
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      const int cc = col0 + (k * THREADS + tid) * VE;
+      if (cc + VE <= m) {
+#pragma unroll
+        for (int e = 0; e < VE; e += 4)
+          *reinterpret_cast<float4*>(slot + cc + e) =
+              make_float4(cacc[k][e], cacc[k][e + 1], cacc[k][e + 2], cacc[k][e + 3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VE; ++e)
+          if (cc + e < m) slot[cc + e] = cacc[k][e];
+      }
+    }
+    if (cr == 0 && tid == ftid) {
+      p.err_part[2 * cid] = double(err_num) - double(err_num_c);
+      p.err_part[2 * cid + 1] = double(err_den) - double(err_den_c);
+    }
+  } else if (done_rows > 0) {
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
       const int cc = col0 + (k * THREADS + tid) * VE;
@@ -413,7 +440,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
       }
     }
   }
-  if (p.track && cr == 0 && tid == ftid && done_rows > 0) {
+  if (p.track && !p.det && cr == 0 && tid == ftid && done_rows > 0) {
     atomicAdd(&p.err_next[0], double(err_num) - double(err_num_c));
     atomicAdd(&p.err_next[1], double(err_den) - double(err_den_c));
   }
@@ -421,8 +448,9 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
 
   // beta_t = (b_j / c_j)^fi for the next pass (kernel form: V <- V beta_t),
   // computed once per column by the CTAs that finish last, in slices, after
-  // every CTA's column partials have landed.
-  {
+  // every CTA's column partials have landed (deterministic mode: by the
+  // reduction launch that follows the pass).
+  if (!p.det) {
     const int nsl = BETA_SLICES;
     const int per = (m + nsl - 1) / nsl;
     uint32_t st2 = 0;

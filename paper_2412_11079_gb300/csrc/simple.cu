@@ -144,6 +144,23 @@ __global__ void __launch_bounds__(TB) kform_plan_kernel(const TK* __restrict__ K
     Elem<TP>::store1(P + int64_t(i) * ldp + j, U[i] * Elem<TK>::load1(K + int64_t(i) * ldk + j) * v);
 }
 
+// uot_sinkhorn's kernel-form storage, last sweep: the buffer holds K, and
+// every entry becomes (U_i K_ij) V_j in place (the product in the order of
+// kform_plan_kernel).
+template <typename T>
+__global__ void __launch_bounds__(TB) kform_materialize_kernel(T* P, int64_t ldp,
+                                                               const float* __restrict__ U,
+                                                               const float* __restrict__ V,
+                                                               int n, int m) {
+  const int j = blockIdx.x * TB + threadIdx.x;
+  if (j >= m) return;
+  const float v = V[j];
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    T* q = P + int64_t(i) * ldp + j;
+    Elem<T>::store1(q, U[i] * Elem<T>::load1(q) * v);
+  }
+}
+
 // Kernel form: U = u0 (the inverse of K's storage scale), V = 1 (zero-padded).
 __global__ void kform_reset_kernel(float* U, int n, float u0, float* V_ws, int m, int mpad) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -364,6 +381,16 @@ cudaError_t launch_kform_plan(const void* K, int64_t ldk, int k_dtype, const flo
           reinterpret_cast<const TK*>(K), ldk, U, V, n, m, reinterpret_cast<TP*>(P), ldp);
       return last();
     });
+  });
+}
+
+cudaError_t launch_kform_materialize(void* P, int64_t ldp, int dtype, const float* U,
+                                     const float* V, int n, int m, cudaStream_t s) {
+  return by_dtype(dtype, [&](auto z) {
+    using T = decltype(z);
+    kform_materialize_kernel<T><<<col_grid(n, m), TB, 0, s>>>(reinterpret_cast<T*>(P), ldp, U, V,
+                                                              n, m);
+    return last();
   });
 }
 

@@ -27,6 +27,11 @@ struct Control {
   double pad[5];
 };
 
+// Deterministic mode: at most this many row groups (one per CTA, or per
+// cluster when a row spans several CTAs) in a pass, each with its own slot of
+// column partial sums.
+constexpr int DET_SLOTS = 304;
+
 // Offsets (bytes) of the workspace regions for an n x m problem.
 struct WsLayout {
   size_t ctl;     // Control
@@ -39,13 +44,16 @@ struct WsLayout {
   size_t ctr;     // int32[9]: per-pass row, arrival and slice counters, rings of 3
   size_t beta;    // float[mpad]: column factors of the last completed pass
   size_t log2k;   // double: log2 of the fixed-point row factor (kernel-form gauge)
+  size_t u;       // float[npad]: row scalings U of uot_sinkhorn's kernel-form storage
+  size_t part;    // float[DET_SLOTS][mpad]: deterministic mode, column partials per slot
+  size_t err_part;// double[DET_SLOTS][2]: deterministic mode, stopping-error partials
   size_t total;
   int64_t mpad, npad;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-inline WsLayout ws_layout(int64_t n, int64_t m) {
+inline WsLayout ws_layout(int64_t n, int64_t m, bool det = false) {
   WsLayout L{};
   L.mpad = (m + 63) & ~int64_t(63);
   L.npad = (n + 63) & ~int64_t(63);
@@ -60,6 +68,11 @@ inline WsLayout ws_layout(int64_t n, int64_t m) {
   L.ctr = off; off = align256(off + 9 * sizeof(int32_t));
   L.beta = off; off = align256(off + size_t(L.mpad) * 4);
   L.log2k = off; off = align256(off + sizeof(double));
+  L.u = off; off = align256(off + size_t(L.npad) * 4);
+  L.part = off;
+  if (det) off = align256(off + size_t(DET_SLOTS) * size_t(L.mpad) * 4);
+  L.err_part = off;
+  if (det) off = align256(off + size_t(DET_SLOTS) * 2 * sizeof(double));
   L.total = off;
   return L;
 }
@@ -105,6 +118,9 @@ struct FusedArgs {
   float* save_V;       // V_t (m)
   int pot;             // kernel form: scaling-vector rule (uot_rule POT)
   float kscale;        // kernel form: storage scale of K (2^s; FP16 K is stored x 2^15)
+  int det;             // 1: deterministic mode (static rows, partials to slots)
+  float* part;         // deterministic: column partials, slot g at part + g * mpad
+  double* err_part;    // deterministic: stopping-error partials, slot g at 2 * g
 };
 
 // History of a kernel-form solve kept for the adjoint: a header, then for
@@ -151,6 +167,11 @@ int fused_pick(int dtype, int64_t m, int tile);
 cudaError_t fused_geometry(bool kf, int k, int cs, int n, int* grid, int* stages, size_t* smem);
 cudaError_t fused_launch(bool kf, int k, int cs, int grid, size_t smem, bool tma,
                          const FusedArgs& args, cudaStream_t s);
+// Deterministic mode: after a pass over `groups` row groups, adds the column
+// partial slots in slot order into the column sums of iteration t, forms the
+// next column factors (kernel form: the new V), and adds the stopping-error
+// slots in order.
+cudaError_t det_reduce_launch(bool kf, int groups, const FusedArgs& args, cudaStream_t s);
 
 // Simple kernels (simple.cu).
 cudaError_t launch_init(const float* C, int64_t ldc, void* P, int64_t ldp, int n, int m,
@@ -163,6 +184,8 @@ cudaError_t launch_kform_finish(float* V, int m, int iters, const uint8_t* ws, W
 cudaError_t launch_kform_plan(const void* K, int64_t ldk, int k_dtype, const float* U,
                               const float* V, int n, int m, void* P, int64_t ldp, int p_dtype,
                               cudaStream_t s);
+cudaError_t launch_kform_materialize(void* P, int64_t ldp, int dtype, const float* U,
+                                     const float* V, int n, int m, cudaStream_t s);
 cudaError_t launch_kform_cost(const void* K, int64_t ldk, int k_dtype, const float* U,
                               const float* V, const float* C, int64_t ldc, int n, int m,
                               double* out, cudaStream_t s);

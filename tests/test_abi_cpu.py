@@ -41,12 +41,16 @@ def test_status_strings_and_defaults(lib):
     lib.uot_default_options(ctypes.byref(o))
     assert (o.dtype, o.algo, o.check_every, o.tile, o.cluster, o.max_ctas, o.rule) == \
         (0, 0, 1, 0, 0, 0, uot.UOT_RULE_PAPER)
+    assert (o.storage, o.deterministic) == (uot.UOT_STORAGE_INPLACE, 0)
 
 
 def test_workspace_size(lib):
     from paper_2412_11079_gb300 import uot
     s = uot.uot_workspace_size(16384, 16384)
     assert s % 256 == 0 and s >= 3 * 16384 * 4 + 16384 * 4
+    # deterministic mode: one slot of column partials per row group (304 slots)
+    d = uot.uot_workspace_size(16384, 16384, uot.options(deterministic=True))
+    assert d % 256 == 0 and d >= s + 304 * 16384 * 4
     assert uot.uot_workspace_size(0, 5) == 0
     assert uot.uot_workspace_size(5, -1) == 0
 
@@ -104,6 +108,17 @@ def test_argument_validation_needs_no_gpu(lib):
     assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 1 << 20,
              ctypes.byref(uot.options(rule=uot.UOT_RULE_POT)), None,
              None) == uot.UOT_ERR_UNSUPPORTED
+    # storage and deterministic: unknown values; neither exists for the multi-pass
+    # baseline
+    for field, val in [("storage", 2), ("deterministic", 2), ("storage", -1)]:
+        bad = uot.options()
+        setattr(bad, field, val)
+        assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 1 << 20, ctypes.byref(bad), None,
+                 None) == uot.UOT_ERR_INVALID_ARG
+    for kw in [dict(storage=uot.UOT_STORAGE_KFORM), dict(deterministic=True)]:
+        mp = uot.options(algo=uot.UOT_ALGO_MULTIPASS, **kw)
+        assert f(P, 4, P, P, 4, 4, 0.1, 1.0, 5, 0.0, P, 1 << 20, ctypes.byref(mp), None,
+                 None) == uot.UOT_ERR_UNSUPPORTED
     g = lib.uot_init_kernel
     assert g(None, 4, P, 4, 4, 4, 0.1, None, None) == uot.UOT_ERR_INVALID_ARG
     assert g(P, 4, P, 4, 4, 4, -1.0, None, None) == uot.UOT_ERR_INVALID_ARG

@@ -20,7 +20,6 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-5
-RUN_TOL_500 = 4e-5  # two GPU runs of 500 FP32 iterations (see test_large_case_full_size)
 
 
 @pytest.fixture(scope="module")
@@ -283,9 +282,12 @@ def test_large_case_full_size(uot):
     """N=M=16384 FP32 (1 GiB plan), 64-D Gaussian clouds, reg 0.1, reg_m 0.5,
     in the launch configuration the benchmark times: (1) three iterations from
     P0 against the oracle element by element; (2) 499 + 1 iterations equal 500
-    (state is the plan alone); (3) the 500th iteration, from the GPU's own
-    state, against one oracle iteration from that state."""
-    p = workloads.large_case(seed=0)
+    (the state between calls is the plan alone), in deterministic mode so
+    that the two solves differ only by where the 499th column factor is
+    applied; (3) the 500th iteration, from the GPU's own state, against one
+    oracle iteration from that state.  The full 500 iterations from P0 are
+    compared with the oracle at 2048 x 16384 (test_gpu_storage_det.py)."""
+    p = workloads.large_case(seed=0, n=16384, m=16384)
     n, m = p.C.shape
     C, a, b = dev(p.C), dev(p.a), dev(p.b)
     plan = torch.empty((n, m), device="cuda")
@@ -298,24 +300,20 @@ def test_large_case_full_size(uot):
     assert rel_err(got3, ref3) <= FP32_TOL
     del got3, ref3
 
+    det = uot.options(deterministic=True)
+    wsd = uot.workspace(n, m, det)
     uot.uot_init_kernel(C, plan, p.reg)
-    uot.uot_sinkhorn(plan, a, b, p.reg, p.reg_m, 499, ws=ws)
+    uot.uot_sinkhorn(plan, a, b, p.reg, p.reg_m, 499, ws=wsd, opt=det)
     state = plan.clone()
-    uot.uot_sinkhorn(plan, a, b, p.reg, p.reg_m, 1, ws=ws)
+    uot.uot_sinkhorn(plan, a, b, p.reg, p.reg_m, 1, ws=wsd, opt=det)
     last = plan.clone()
     uot.uot_init_kernel(C, plan, p.reg)
-    full = uot.uot_sinkhorn(plan, a, b, p.reg, p.reg_m, 500, ws=ws)
+    full = uot.uot_sinkhorn(plan, a, b, p.reg, p.reg_m, 500, ws=wsd, opt=det)
     assert full.iters_done == 500 and full.dev_status == 0
     assert torch.isfinite(plan).all().item()
     d = ((plan.double() - last.double()).abs() /
          torch.clamp(last.double().abs(), min=1e-6 * last.abs().max().item())).max().item()
-    # Two GPU runs add each column's partial sums in different orders (the
-    # dynamic row schedule and the atomic folding vary between runs): a
-    # relative difference of about fi * u * sqrt(rows per CTA) ~ 5e-7 in a
-    # column factor per iteration (u = 2^-24, ~108 rows per CTA), a random
-    # walk of ~1.1e-5 over 500 iterations.  Carried state other than the plan
-    # would differ at order 1e-1.
-    assert d <= RUN_TOL_500
+    assert d <= FP32_TOL
     S = state.double().cpu().numpy()
     one = oracle.sinkhorn(S, p.a, p.b, p.reg, p.reg_m, 1).plan
     assert rel_err(last.double().cpu().numpy(), one) <= FP32_TOL
