@@ -32,6 +32,8 @@ def test_reference_arm_json_line():
     assert line["higher_is_better"] is True and line["vs_baseline"] is None
     assert line["config"]["n"] == 128 and line["config"]["m"] == 96
     assert "workload" in line["config"]
+    # the line describes the oracle it timed, not the GPU path
+    assert line["config"]["plan_dtype"] == "f64" and "oracle" in line["config"]["algo"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     assert cb["sample"]
