@@ -72,8 +72,9 @@ typedef enum uot_algo { UOT_ALGO_FUSED = 0, UOT_ALGO_MULTIPASS = 1 } uot_algo;
  *        this is the PAPER factor times u_i^(fi - 1).  Its limit minimises
  *        <P,C> + reg sum P (log P - 1) + reg_m KL(P 1 | a) + reg_m KL(P^T 1 | b).
  *        Only the kernel form keeps u and v, so only the kernel-form entry
- *        points and the batched engines accept it; the two rules agree when
- *        fi = 1.  The adjoint (uot_sinkhorn_backward) is for PAPER only. */
+ *        points, uot_sinkhorn with UOT_STORAGE_KFORM and the batched engines
+ *        accept it; the two rules agree when fi = 1.  The adjoint
+ *        (uot_sinkhorn_backward) is for PAPER only. */
 typedef enum uot_rule { UOT_RULE_PAPER = 0, UOT_RULE_POT = 1 } uot_rule;
 
 /* How uot_sinkhorn keeps the plan during the iterations (both give the plan
@@ -182,6 +183,10 @@ uot_status uot_init_kernel(const float* C, int64_t ldc, void* plan, int64_t ldp,
  * fi = 1 (balanced Sinkhorn).  The fused algorithm runs one plan sweep per
  * iteration plus one final sweep that applies the last column factor, so on
  * return `plan` holds the plan after the column step of the last iteration.
+ * opt->storage chooses how the plan is kept during the iterations
+ * (uot_storage: rewritten in place by every pass, or kept as K with FP32
+ * scalings and written once at the end); opt->deterministic makes the result
+ * bit-identical from run to run.
  * Degenerate factors: target 0 gives factor 0; a zero sum with a positive
  * target gives factor 1 and UOT_DEV_ZERO_SUM.
  * Stopping (the paper leaves the error undefined): when tol > 0, after every
@@ -289,7 +294,10 @@ uot_status uot_sinkhorn_kform_save(const void* K, int64_t ldk, const float* a, c
  *   w = -fi G / c_t,  db += fi G / b,  F += Q_t w,  G = (1 - fi) G,
  *   z = -fi F / r_t,  da += fi F / a,  G += R_t^T z, F = (1 - fi) F,
  * with dl += Q_t * w + R_t * z accumulated in the dC buffer, starting from
- * dl = P_T * C; finally dC = grad_out (P_T - dl / reg).  K and dC must be
+ * dl = P_T * C; finally dC = g (P_T - dl / reg), da and db times g, where
+ * g = grad_out, times *grad_out_dev when grad_out_dev (one device double,
+ * 8-byte aligned, read by the last launch) is not NULL -- so a caller whose
+ * incoming gradient lives on the device need not synchronise.  K and dC must be
  * 16-byte aligned with ldk and lddc multiples of 4; m <= 8192.  The
  * workspace (uot_backward_workspace_size bytes, 256-byte aligned) is
  * caller-owned.  opt may be NULL; only opt->max_ctas is used.  Asynchronous.
@@ -298,9 +306,9 @@ size_t uot_backward_workspace_size(int64_t n, int64_t m);
 uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, int64_t ldc,
                                  const float* a, const float* b, int64_t n, int64_t m, float reg,
                                  float reg_m, int32_t iters, const void* hist, size_t hist_bytes,
-                                 double grad_out, float* dC, int64_t lddc, float* da, float* db,
-                                 void* workspace, size_t ws_bytes, const uot_options* opt,
-                                 void* stream);
+                                 double grad_out, const double* grad_out_dev, float* dC,
+                                 int64_t lddc, float* da, float* db, void* workspace,
+                                 size_t ws_bytes, const uot_options* opt, void* stream);
 
 /* Synchronises `stream` and reads the result of the last uot_sinkhorn call
  * that used `workspace` (same n, m, opt).  Returns the device status as a

@@ -31,5 +31,6 @@ from .uot import (  # noqa: F401
     sinkhorn_pot,
     transport_cost,
     sinkhorn_grad,
+    sinkhorn_grad_magnitude,
     kernel_form_scalings,
 )

@@ -246,24 +246,11 @@ def sinkhorn_grad(C, a, b, reg: float, reg_m: float, iters: int):
     Finally ``dC = P_T - dl / reg``.  All arithmetic in FP64.  Requires strictly
     positive ``a`` and ``b`` (the log-space form has no degenerate factors).
     """
-    fi = fi_exponent(reg, reg_m)
-    C = np.asarray(C, np.float64)
+    fi, l, f, g, rs, cs = _log_forward(C, a, b, reg, reg_m, iters, "sinkhorn_grad")
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
-    if np.any(a <= 0) or np.any(b <= 0):
-        raise ValueError("sinkhorn_grad needs strictly positive marginals")
-    l = -C / reg
+    C = np.asarray(C, np.float64)
     N, M = C.shape
-    f = [np.zeros(N)]
-    g = [np.zeros(M)]
-    rs, cs = [], []
-    for _ in range(iters):
-        r = np.exp(l + f[-1][:, None] + g[-1][None, :]).sum(axis=1)
-        f.append(f[-1] + fi * (np.log(a) - np.log(r)))
-        c = np.exp(l + f[-1][:, None] + g[-1][None, :]).sum(axis=0)
-        g.append(g[-1] + fi * (np.log(b) - np.log(c)))
-        rs.append(r)
-        cs.append(c)
     P = np.exp(l + f[-1][:, None] + g[-1][None, :])
     value = float(np.sum(P * C))
     dl = P * C
@@ -286,3 +273,62 @@ def sinkhorn_grad(C, a, b, reg: float, reg_m: float, iters: int):
         F = (1.0 - fi) * F
     dC = P - dl / reg
     return value, dC, da, db
+
+
+def _log_forward(C, a, b, reg: float, reg_m: float, iters: int, who: str):
+    """The log-space forward of ``sinkhorn_grad``: ``fi``, ``l = -C/reg`` and
+    the lists ``f_t``, ``g_t`` (t = 0..iters), ``r_t``, ``c_t`` (t = 1..iters)."""
+    fi = fi_exponent(reg, reg_m)
+    C = np.asarray(C, np.float64)
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if np.any(a <= 0) or np.any(b <= 0):
+        raise ValueError(f"{who} needs strictly positive marginals")
+    l = -C / reg
+    N, M = C.shape
+    f = [np.zeros(N)]
+    g = [np.zeros(M)]
+    rs, cs = [], []
+    for _ in range(iters):
+        r = np.exp(l + f[-1][:, None] + g[-1][None, :]).sum(axis=1)
+        f.append(f[-1] + fi * (np.log(a) - np.log(r)))
+        c = np.exp(l + f[-1][:, None] + g[-1][None, :]).sum(axis=0)
+        g.append(g[-1] + fi * (np.log(b) - np.log(c)))
+        rs.append(r)
+        cs.append(c)
+    return fi, l, f, g, rs, cs
+
+
+def sinkhorn_grad_magnitude(C, a, b, reg: float, reg_m: float, iters: int):
+    """Magnitudes of the terms each gradient entry of ``sinkhorn_grad`` is
+    formed from: the same reverse recurrence with every term taken by its
+    absolute value (``w = +fi G / c``, ``z = +fi F / r`` on the magnitudes,
+    ``dC = P + dl / reg``).  Rounding errors of any evaluation of the adjoint
+    scale with these, not with the gradient itself, which can be far smaller
+    where terms of opposite sign cancel.  Returns ``(dC_mag, da_mag, db_mag)``,
+    each elementwise >= the absolute value of the gradient."""
+    fi, l, f, g, rs, cs = _log_forward(C, a, b, reg, reg_m, iters, "sinkhorn_grad_magnitude")
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    C = np.asarray(C, np.float64)
+    N, M = C.shape
+    P = np.exp(l + f[-1][:, None] + g[-1][None, :])
+    dl = P * np.abs(C)
+    F = dl.sum(axis=1)
+    G = dl.sum(axis=0)
+    da = np.zeros(N)
+    db = np.zeros(M)
+    for t in range(iters, 0, -1):
+        Q = np.exp(l + f[t][:, None] + g[t - 1][None, :])
+        R = np.exp(l + f[t - 1][:, None] + g[t - 1][None, :])
+        w = fi * G / cs[t - 1]
+        db += fi * G / b
+        F = F + Q @ w
+        dl += Q * w[None, :]
+        G = (1.0 - fi) * G
+        z = fi * F / rs[t - 1]
+        da += fi * F / a
+        G = G + R.T @ z
+        dl += R * z[:, None]
+        F = (1.0 - fi) * F
+    return P + dl / reg, da, db

@@ -33,8 +33,11 @@ class UOTSinkhorn(torch.autograd.Function):
     def backward(ctx, grad_out):
         C, a, b, K, hist = ctx.saved_tensors
         reg, reg_m, iters = ctx.params
-        dC, da, db = uot.uot_sinkhorn_backward(K, C, a, b, reg, reg_m, iters, hist,
-                                               float(grad_out))
+        # The incoming gradient stays on the device (no host synchronisation,
+        # so the backward can sit inside a captured step).
+        g = grad_out.detach().to(torch.float64).reshape(1).contiguous()
+        dC, da, db = uot.uot_sinkhorn_backward(K, C, a, b, reg, reg_m, iters, hist, 1.0,
+                                               grad_out_dev=g)
         return dC.to(C.dtype), da, db, None, None, None
 
 

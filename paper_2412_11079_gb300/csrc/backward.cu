@@ -329,11 +329,13 @@ __global__ void bw_cols_kernel(const float* G0, const float* cT, const float* b,
   Gs[j] = (1.0f - fi) * G;
 }
 
-// dC = g (P_T - dl / reg), da *= g, db *= g.
+// dC = g (P_T - dl / reg), da *= g, db *= g, with g = grad_out times the
+// optional device scalar (read here, so the caller need not synchronise).
 __global__ void __launch_bounds__(TB) bw_final_kernel(const float* K, int64_t ldk, const float* U,
                                                       const float* V, float* D, int64_t ldd,
-                                                      int n, int m, float inv_reg, float g,
-                                                      float* da, float* db) {
+                                                      int n, int m, float inv_reg, double g_host,
+                                                      const double* g_dev, float* da, float* db) {
+  const float g = float(g_dev ? g_host * *g_dev : g_host);
   const int j = blockIdx.x * TB + threadIdx.x;
   if (blockIdx.y == 0) {
     for (int i = j; i < n; i += gridDim.x * TB) da[i] *= g;
@@ -433,9 +435,9 @@ size_t uot_backward_workspace_size(int64_t n, int64_t m) {
 uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, int64_t ldc,
                                  const float* a, const float* b, int64_t n, int64_t m, float reg,
                                  float reg_m, int32_t iters, const void* hist, size_t hist_bytes,
-                                 double grad_out, float* dC, int64_t lddc, float* da, float* db,
-                                 void* workspace, size_t ws_bytes, const uot_options* opt,
-                                 void* stream) {
+                                 double grad_out, const double* grad_out_dev, float* dC,
+                                 int64_t lddc, float* da, float* db, void* workspace,
+                                 size_t ws_bytes, const uot_options* opt, void* stream) {
   const int max_ctas = opt ? opt->max_ctas : 0;
   if (max_ctas < 0) return UOT_ERR_INVALID_ARG;
   if (!K || !C || !a || !b || !hist || !dC || !da || !db || n < 1 || m < 1 || n > INT32_MAX ||
@@ -443,6 +445,7 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
     return UOT_ERR_INVALID_ARG;
   if (!(reg > 0.0f) || !std::isfinite(reg) || !(reg_m > 0.0f) || !std::isfinite(grad_out))
     return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(grad_out_dev) % 8) return UOT_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(K) % 16 || reinterpret_cast<uintptr_t>(dC) % 16 ||
       ldk % 4 || lddc % 4)
     return UOT_ERR_INVALID_ARG;  // rows of K and dC are fetched with bulk copies
@@ -581,7 +584,7 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
     int gy = (sms * 8 + gx - 1) / gx;
     gy = std::max(1, std::min(gy, std::min(N, 65535)));
     bw_final_kernel<<<dim3(gx, gy), TB, 0, s>>>(K, ldk, U_t(T), V_t(T), dC, lddc, N, M, 1.0f / reg,
-                                              float(grad_out), da, db);
+                                              grad_out, grad_out_dev, da, db);
     if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
     count_launch();
   }

@@ -97,7 +97,7 @@ SIGNATURES = {
                                                ctypes.POINTER(UotResult)]),
     "uot_backward_workspace_size": (_SZ, [_I64, _I64]),
     "uot_sinkhorn_backward": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _P, _I64, _I64, _F, _F,
-                                             _I32, _P, _SZ, _D, _P, _I64, _P, _P, _P, _SZ,
+                                             _I32, _P, _SZ, _D, _P, _P, _I64, _P, _P, _P, _SZ,
                                              ctypes.POINTER(UotOptions), _P]),
     "uot_sinkhorn_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _D,
                                             ctypes.POINTER(UotOptions), _P,
@@ -500,8 +500,17 @@ def uot_sinkhorn_kform_save(K, a, b, reg: float, reg_m: float, iters: int, U=Non
 
 def uot_sinkhorn_backward(K, C, a, b, reg: float, reg_m: float, iters: int, hist,
                           grad_out: float = 1.0, dC=None, da=None, db=None, ws=None,
-                          stream=None, opt: UotOptions | None = None):
+                          stream=None, opt: UotOptions | None = None, grad_out_dev=None):
+    """Adjoint of the solve recorded in `hist`.  The gradients are scaled by
+    grad_out, times the one-element float64 device tensor grad_out_dev if
+    given (read on the device, no synchronisation)."""
     torch = _torch()
+    gdev = None
+    if grad_out_dev is not None:
+        if (not grad_out_dev.is_cuda or grad_out_dev.dtype != torch.float64
+                or grad_out_dev.numel() != 1):
+            raise ValueError("grad_out_dev must be a one-element CUDA float64 tensor")
+        gdev = grad_out_dev.data_ptr()
     n, m = K.shape
     dC = torch.empty((n, (m + 3) // 4 * 4), device=K.device)[:, :m] if dC is None else dC
     da = torch.empty(n, device=K.device) if da is None else da
@@ -513,7 +522,8 @@ def uot_sinkhorn_backward(K, C, a, b, reg: float, reg_m: float, iters: int, hist
     gp, ldd = _matrix(dC, "dC")
     _check(load().uot_sinkhorn_backward(kp, ldk, cp, ldc, _vector(a, "a", n), _vector(b, "b", m),
                                         n, m, float(reg), float(reg_m), int(iters),
-                                        hist.data_ptr(), hist.numel(), float(grad_out), gp, ldd,
+                                        hist.data_ptr(), hist.numel(), float(grad_out), gdev, gp,
+                                        ldd,
                                         _vector(da, "da", n), _vector(db, "db", m),
                                         ws.data_ptr(), ws.numel(),
                                         ctypes.byref(opt) if opt else None, _stream(stream)),

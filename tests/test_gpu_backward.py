@@ -4,10 +4,20 @@ the plain unrolled loop, and the oracle's adjoint.
 
 Inputs follow the differentiation workload: C = squared distances of 16-D
 Gaussian clouds divided by max(C), a/b uniform(0.5, 1.5) normalised to 1.0 /
-1.5, reg 0.05, reg_m 1.0, 200 iterations.  Tolerance: the GPU runs the
-forward and 2T reverse sweeps in FP32, so each gradient is compared with
-max|g - g*| <= 2e-4 max|g*| (the FP32 unit roundoff 6e-8 times the 2T+1 =
-401 sweeps is 2.4e-5; the bound leaves room for the reductions' growth).
+1.5, reg 0.05, reg_m 1.0, 200 iterations.
+
+Tolerance, per element: each gradient entry is a sum of terms of both signs
+(dC = P_T - dl / reg with dl collecting P_T C and every reverse step's
+Q_t w and R_t z; da and db collect the row and column adjoints of every
+step), so where they cancel the entry is far smaller than its terms and its
+relative error is not bounded by the arithmetic.  FP32 rounding errors scale
+with the terms' magnitudes instead, which the oracle computes by running the
+same reverse recurrence on absolute values (sinkhorn_grad_magnitude).  The
+GPU runs one FP32 forward (errors of the scalings about 1e-6 relative after
+hundreds of iterations) and 2T reverse sweeps, each adding terms rounded to
+u = 2^-24 of their size: |g - g*| <= (2T + 1) u mag per entry, 2.4e-5 mag at
+T = 200 before reduction growth.  The test allows GRAD_TOL = 1e-4 of the
+magnitude (floor 1e-6 of the largest), per entry.
 """
 
 import numpy as np
@@ -19,7 +29,7 @@ from paper_2412_11079_gb300 import workloads
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-GRAD_TOL = 2e-4
+GRAD_TOL = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -48,9 +58,16 @@ def gpu_grads(ag, p):
             b.grad.double().cpu().numpy())
 
 
-def close(g, ref, tol=GRAD_TOL):
-    err = np.max(np.abs(g - ref)) / np.max(np.abs(ref))
+def close(g, ref, mag, tol=GRAD_TOL):
+    """Per entry: |g - ref| <= tol * max(mag, 1e-6 max(mag))."""
+    err = np.max(np.abs(g - ref) / np.maximum(mag, 1e-6 * np.max(mag)))
     assert err <= tol, err
+
+
+def magnitudes(p, iters=None, scale=1.0):
+    m = oracle.sinkhorn_grad_magnitude(p.C, p.a, p.b, p.reg, p.reg_m,
+                                       p.iters if iters is None else iters)
+    return tuple(scale * x for x in m)
 
 
 def test_grad_vs_finite_differences_16(ag):
@@ -75,9 +92,10 @@ def test_grad_vs_finite_differences_16(ag):
                     for e in np.eye(16)])
     fdb = np.array([(L(C64, a64, b64 + h * e) - L(C64, a64, b64 - h * e)) / (2 * h)
                     for e in np.eye(16)])
-    close(dC, fdC)
-    close(da, fda)
-    close(db, fdb)
+    mC, ma, mb = magnitudes(p)
+    close(dC, fdC, mC)
+    close(da, fda, ma)
+    close(db, fdb, mb)
 
 
 def test_grad_vs_torch_fp64_autograd_256(ag):
@@ -94,9 +112,10 @@ def test_grad_vs_torch_fp64_autograd_256(ag):
     loss = (P * Ct).sum()
     loss.backward()
     assert abs(val - loss.item()) <= 1e-5 * abs(loss.item())
-    close(dC, Ct.grad.numpy())
-    close(da, at.grad.numpy())
-    close(db, bt.grad.numpy())
+    mC, ma, mb = magnitudes(p)
+    close(dC, Ct.grad.numpy(), mC)
+    close(da, at.grad.numpy(), ma)
+    close(db, bt.grad.numpy(), mb)
 
 
 @pytest.mark.slow
@@ -105,9 +124,10 @@ def test_grad_vs_oracle_adjoint_512(ag):
     val, dC, da, db = gpu_grads(ag, p)
     ref_val, rdC, rda, rdb = oracle.sinkhorn_grad(p.C, p.a, p.b, p.reg, p.reg_m, p.iters)
     assert abs(val - ref_val) <= 1e-5 * abs(ref_val)
-    close(dC, rdC)
-    close(da, rda)
-    close(db, rdb)
+    mC, ma, mb = magnitudes(p)
+    close(dC, rdC, mC)
+    close(da, rda, ma)
+    close(db, rdb, mb)
 
 
 def test_grad_full_size_few_iterations(ag):
@@ -116,9 +136,24 @@ def test_grad_full_size_few_iterations(ag):
     val, dC, da, db = gpu_grads(ag, p)
     ref_val, rdC, rda, rdb = oracle.sinkhorn_grad(p.C, p.a, p.b, p.reg, p.reg_m, p.iters)
     assert abs(val - ref_val) <= 1e-5 * abs(ref_val)
-    close(dC, rdC)
-    close(da, rda)
-    close(db, rdb)
+    mC, ma, mb = magnitudes(p)
+    close(dC, rdC, mC)
+    close(da, rda, ma)
+    close(db, rdb, mb)
+
+
+@pytest.mark.slow
+def test_grad_workload_configuration_200_iterations(ag):
+    """One problem of the timed configuration: N=M=2048, all 200 unrolled
+    iterations, forward and adjoint, against the oracle's FP64 adjoint."""
+    p = case(2048, iters=200, seed=7)
+    val, dC, da, db = gpu_grads(ag, p)
+    ref_val, rdC, rda, rdb = oracle.sinkhorn_grad(p.C, p.a, p.b, p.reg, p.reg_m, p.iters)
+    assert abs(val - ref_val) <= 1e-5 * abs(ref_val)
+    mC, ma, mb = magnitudes(p)
+    close(dC, rdC, mC)
+    close(da, rda, ma)
+    close(db, rdb, mb)
 
 
 def test_grad_ragged_shape_and_grad_out(ag):
@@ -129,6 +164,30 @@ def test_grad_ragged_shape_and_grad_out(ag):
     b = torch.from_numpy(p.b).cuda().requires_grad_(True)
     (2.5 * ag.sinkhorn_cost(C, a, b, p.reg, p.reg_m, p.iters)).backward()
     ref_val, rdC, rda, rdb = oracle.sinkhorn_grad(p.C, p.a, p.b, p.reg, p.reg_m, p.iters)
-    close(C.grad.double().cpu().numpy(), 2.5 * rdC)
-    close(a.grad.double().cpu().numpy(), 2.5 * rda)
-    close(b.grad.double().cpu().numpy(), 2.5 * rdb)
+    mC, ma, mb = magnitudes(p, scale=2.5)
+    close(C.grad.double().cpu().numpy(), 2.5 * rdC, mC)
+    close(a.grad.double().cpu().numpy(), 2.5 * rda, ma)
+    close(b.grad.double().cpu().numpy(), 2.5 * rdb, mb)
+
+
+def test_backward_takes_grad_out_on_the_device(ag):
+    """The device scalar multiplies the host grad_out (0.5 * -3 here), with no
+    host read of it; the result is the oracle's gradient times -1.5."""
+    from paper_2412_11079_gb300 import uot
+    p = workloads.gauss_normalised(4, 64, 96, 16, 0.1, 0.7, 20, 1.0, 1.5, "uniform")
+    n, m = p.C.shape
+    C = torch.from_numpy(p.C).cuda()
+    a = torch.from_numpy(p.a).cuda()
+    b = torch.from_numpy(p.b).cuda()
+    K = torch.empty((n, m), device="cuda")
+    uot.uot_init_kernel(C, K, p.reg)
+    U, V, hist = uot.uot_sinkhorn_kform_save(K, a, b, p.reg, p.reg_m, p.iters)
+    g = torch.tensor([-3.0], dtype=torch.float64, device="cuda")
+    dC, da, db = uot.uot_sinkhorn_backward(K, C, a, b, p.reg, p.reg_m, p.iters, hist, 0.5,
+                                           grad_out_dev=g)
+    torch.cuda.synchronize()
+    _, rdC, rda, rdb = oracle.sinkhorn_grad(p.C, p.a, p.b, p.reg, p.reg_m, p.iters)
+    mC, ma, mb = magnitudes(p, scale=1.5)
+    close(dC.double().cpu().numpy(), -1.5 * rdC, mC)
+    close(da.double().cpu().numpy(), -1.5 * rda, ma)
+    close(db.double().cpu().numpy(), -1.5 * rdb, mb)

@@ -271,6 +271,45 @@ def test_grad_matches_torch_autograd(N, M, T):
     np.testing.assert_allclose(db, bt.grad.numpy(), rtol=1e-8, atol=1e-12 * np.abs(db).max())
 
 
+def test_grad_magnitude_closed_forms_1x1():
+    """Magnitudes of the adjoint's terms for one entry, by hand.  T = 0:
+    dC = P - P C / reg from terms P and P C / reg.  T = 1: the value is
+    dC = P - (1-fi)^2 P C / reg, da = fi (1-fi) P C / a, db = fi P C / b;
+    the column step's correction -fi P C and the row step's -fi (1-fi) P C
+    count positively in the magnitudes, which become P + (1+fi)^2 P C / reg,
+    fi (1+fi) P C / a and fi P C / b."""
+    C = np.array([[0.7]])
+    a, b = np.array([0.3]), np.array([1.9])
+    reg, reg_m = 0.5, 0.8
+    fi = oracle.fi_exponent(reg, reg_m)
+    dC0, da0, db0 = oracle.sinkhorn_grad_magnitude(C, a, b, reg, reg_m, 0)
+    P0 = np.exp(-0.7 / reg)
+    assert dC0[0, 0] == pytest.approx(P0 + P0 * 0.7 / reg, rel=1e-14)
+    assert da0[0] == 0.0 and db0[0] == 0.0
+    val, dC, da, db = oracle.sinkhorn_grad(C, a, b, reg, reg_m, 1)
+    P = oracle.sinkhorn(oracle.init_plan(C, reg), a, b, reg, reg_m, 1).plan[0, 0]
+    PC = P * 0.7
+    assert dC[0, 0] == pytest.approx(P - (1 - fi) ** 2 * PC / reg, rel=1e-12)
+    assert da[0] == pytest.approx(fi * (1 - fi) * PC / 0.3, rel=1e-12)
+    assert db[0] == pytest.approx(fi * PC / 1.9, rel=1e-12)
+    mC, ma, mb = oracle.sinkhorn_grad_magnitude(C, a, b, reg, reg_m, 1)
+    assert mC[0, 0] == pytest.approx(P + (1 + fi) ** 2 * PC / reg, rel=1e-12)
+    assert ma[0] == pytest.approx(fi * (1 + fi) * PC / 0.3, rel=1e-12)
+    assert mb[0] == pytest.approx(fi * PC / 1.9, rel=1e-12)
+
+
+def test_grad_magnitude_dominates_gradient():
+    """Every entry's magnitude bounds the gradient entry (triangle
+    inequality), and exceeds it by far where terms cancel."""
+    C, a, b = rand_problem(18, 20, 15)
+    for reg, reg_m, T in [(0.2, 1.0, 25), (0.1, 0.3, 10), (0.3, math.inf, 15)]:
+        _, dC, da, db = oracle.sinkhorn_grad(C, a, b, reg, reg_m, T)
+        mC, ma, mb = oracle.sinkhorn_grad_magnitude(C, a, b, reg, reg_m, T)
+        for g, mg in ((dC, mC), (da, ma), (db, mb)):
+            assert np.all(np.abs(g) <= mg * (1 + 1e-12))
+        assert np.max(mC / np.abs(dC)) > 10.0
+
+
 # --- the scaling-vector (POT) form of the unbalanced iteration -------------
 
 
