@@ -164,6 +164,21 @@ uot_status uot_selftest_wait(const int32_t* counter_dev, int32_t target, int32_t
                              double limit_s, uint32_t* status_dev, void* stream);
 
 /*
+ * uot_selftest_factor -- evaluates the rescaling factor of Section 2.1,
+ * (target / total)^fi, exactly as every pass of the library does (FP32
+ * division, then the fast power intrinsic; degenerate readings: target 0
+ * gives 0, a zero total with a positive target gives 1 and UOT_DEV_ZERO_SUM,
+ * a non-finite total or factor sets UOT_DEV_NONFINITE), for `count` pairs:
+ * out[k] from target[k] and total[k] (device FP32 arrays, 4-byte aligned),
+ * with the status bits OR-ed into *status_dev (one device uint32, which the
+ * caller clears).  For checking the factor's accuracy against a reference
+ * power.  Asynchronous.  Errors: UOT_ERR_INVALID_ARG (NULL or misaligned
+ * pointers, count < 1 or > 2^30, fi outside (0, 1]), UOT_ERR_CUDA.
+ */
+uot_status uot_selftest_factor(const float* target, const float* total, int64_t count, float fi,
+                               float* out, uint32_t* status_dev, void* stream);
+
+/*
  * uot_init_kernel -- initial plan P0_ij = exp(-C_ij / reg).
  * Section 2.1 starts from a "given matrix"; the Gibbs kernel of the cost is
  * the usual one for entropic transport.  C: n x m FP32, leading dimension ldc.
@@ -432,11 +447,15 @@ uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uo
  * streams), fully asynchronous (capturable in a CUDA graph once prepared). */
 uot_status uot_sinkhorn_batched(void* workspace, void* stream);
 
-/* Where prepare put each problem: cluster[i] = the on-chip cluster size
- * (1..16) or 0 for the streaming engine, for i < min(nprob, prepared count).
- * Host only; returns the prepared count, or -1 for a workspace that was never
- * prepared.  `cluster` may be NULL. */
-int32_t uot_batched_placement(const void* workspace, int32_t nprob, int32_t* cluster);
+/* Where prepare put each problem, for i < min(nprob, prepared count):
+ * cluster[i] = the on-chip cluster size (1..16) or 0 for the streaming
+ * engine; team[i] = the size of the streaming team class the problem was
+ * assigned to (a power of two; its team may later split into smaller teams
+ * when the class's queue runs dry) or 0 for an on-chip problem.  Host only;
+ * returns the prepared count, or -1 for a workspace that was never prepared.
+ * `cluster` and `team` may be NULL. */
+int32_t uot_batched_placement(const void* workspace, int32_t nprob, int32_t* cluster,
+                              int32_t* team);
 
 /* Synchronises `stream` and copies each problem's result to out[0..nprob). */
 uot_status uot_batched_results(const void* workspace, int32_t nprob, uot_result* out,

@@ -71,6 +71,10 @@ class Batch:
         """On-chip cluster size per problem (0: streaming engine)."""
         return uot.uot_batched_placement(self.ws, len(self.descs))
 
+    def teams(self):
+        """Streaming team size class per problem (0: on chip)."""
+        return uot.uot_batched_placement(self.ws, len(self.descs), teams=True)[1]
+
     def results(self, stream=None, check_status=True):
         return uot.uot_batched_results(self.ws, len(self.descs), stream, check_status)
 

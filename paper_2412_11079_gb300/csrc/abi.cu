@@ -94,6 +94,19 @@ uot_status uot_selftest_wait(const int32_t* counter_dev, int32_t target, int32_t
   return e == cudaSuccess ? UOT_OK : UOT_ERR_CUDA;
 }
 
+uot_status uot_selftest_factor(const float* target, const float* total, int64_t count, float fi,
+                               float* out, uint32_t* status_dev, void* stream) {
+  if (!target || !total || !out || !status_dev || count < 1 || count > (int64_t(1) << 30))
+    return UOT_ERR_INVALID_ARG;
+  if (!(fi > 0.0f) || !(fi <= 1.0f)) return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(target) % 4 || reinterpret_cast<uintptr_t>(total) % 4 ||
+      reinterpret_cast<uintptr_t>(out) % 4 || reinterpret_cast<uintptr_t>(status_dev) % 4)
+    return UOT_ERR_INVALID_ARG;
+  cudaError_t e = launch_factor_selftest(target, total, count, fi, out, status_dev,
+                                         static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? UOT_OK : UOT_ERR_CUDA;
+}
+
 uot_status uot_init_kernel(const float* C, int64_t ldc, void* plan, int64_t ldp, int64_t n,
                            int64_t m, float reg, const uot_options* opt, void* stream) {
   const uot_options o = resolve(opt);

@@ -569,6 +569,7 @@ struct HostPlan {
   int nres;
   ResClass res[MAX_RES_CLASSES];
   std::vector<int8_t> placement;  // per problem: on-chip cluster size, 0 = streaming
+  std::vector<int16_t> team;      // per problem: streaming team size class, 0 = on chip
 };
 static std::mutex g_plan_mu;
 static std::vector<HostPlan> g_plans;
@@ -815,6 +816,7 @@ uot_status uot_batched_prepare(const uot_problem* probs, int32_t nprob, const uo
   for (int c = 0; c < nres; ++c) hp.res[c] = res[c];
   hp.placement.resize(size_t(nprob));
   for (int i = 0; i < nprob; ++i) hp.placement[i] = int8_t(rescls[i] >= 0 ? 1 << rescls[i] : 0);
+  hp.team.assign(gsize.begin(), gsize.end());
   std::lock_guard<std::mutex> lock(g_plan_mu);
   for (HostPlan& h : g_plans)
     if (h.ws == workspace) {
@@ -899,11 +901,14 @@ uot_status uot_batched_results(const void* workspace, int32_t nprob, uot_result*
   return UOT_OK;
 }
 
-int32_t uot_batched_placement(const void* workspace, int32_t nprob, int32_t* cluster) {
+int32_t uot_batched_placement(const void* workspace, int32_t nprob, int32_t* cluster,
+                              int32_t* team) {
   HostPlan hp;
   if (!workspace || !find_plan(workspace, &hp)) return -1;
-  if (cluster)
-    for (int i = 0; i < std::min(nprob, hp.nprob); ++i) cluster[i] = hp.placement[i];
+  for (int i = 0; i < std::min(nprob, hp.nprob); ++i) {
+    if (cluster) cluster[i] = hp.placement[i];
+    if (team) team[i] = hp.team[i];
+  }
   return hp.nprob;
 }
 

@@ -3,6 +3,8 @@
 // workspace reset, and the plain multi-pass form of one iteration (separate
 // row-sum, row-scale, column-sum and column-scale sweeps, the baseline form
 // of Section 2.1 that Section 3.1 analyses).
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "uot_device.cuh"
@@ -460,6 +462,26 @@ __global__ void wait_selftest_kernel(const int* counter, int target, int complet
     }
   }
   status[1] = st;
+}
+
+// Self-test of the rescaling factor: out[k] = rescale_factor(target[k],
+// total[k], fi), the same device function every pass uses, with the
+// degenerate-case status bits OR-ed into *status.
+__global__ void factor_selftest_kernel(const float* target, const float* total, int64_t count,
+                                       float fi, float* out, uint32_t* status) {
+  uint32_t st = 0;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < count;
+       k += int64_t(gridDim.x) * blockDim.x)
+    out[k] = rescale_factor(target[k], total[k], fi, st);
+  if (st) atomicOr(status, st);
+}
+
+cudaError_t launch_factor_selftest(const float* target, const float* total, int64_t count,
+                                   float fi, float* out, uint32_t* status, cudaStream_t s) {
+  const int64_t blocks = std::min<int64_t>((count + TB - 1) / TB, int64_t(sm_count()) * 8);
+  factor_selftest_kernel<<<int(std::max<int64_t>(blocks, 1)), TB, 0, s>>>(target, total, count,
+                                                                          fi, out, status);
+  return last();
 }
 
 cudaError_t launch_wait_selftest(const int* counter, int target, int complete, uint64_t limit_ns,

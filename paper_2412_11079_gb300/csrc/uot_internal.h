@@ -195,6 +195,8 @@ cudaError_t launch_finish(void* P, int64_t ldp, int n, int m, int dtype, const f
 cudaError_t launch_cost(const void* P, int64_t ldp, const float* C, int64_t ldc, int n, int m,
                         int dtype, double* out, cudaStream_t s);
 cudaError_t launch_reset(uint8_t* ws, WsLayout L, const float* b, int m, cudaStream_t s);
+cudaError_t launch_factor_selftest(const float* target, const float* total, int64_t count,
+                                   float fi, float* out, uint32_t* status, cudaStream_t s);
 cudaError_t launch_wait_selftest(const int* counter, int target, int complete, uint64_t limit_ns,
                                  uint32_t* status, cudaStream_t s);
 cudaError_t launch_multipass_iter(void* P, int64_t ldp, int n, int m, int dtype, const float* a,

@@ -76,6 +76,7 @@ SIGNATURES = {
     "uot_workspace_size": (_SZ, [_I64, _I64, ctypes.POINTER(UotOptions)]),
     "uot_launch_count": (ctypes.c_uint64, []),
     "uot_selftest_wait": (ctypes.c_int, [_P, _I32, _I32, _D, _P, _P]),
+    "uot_selftest_factor": (ctypes.c_int, [_P, _P, _I64, _F, _P, _P, _P]),
     "uot_init_kernel": (ctypes.c_int, [_P, _I64, _P, _I64, _I64, _I64, _F,
                                        ctypes.POINTER(UotOptions), _P]),
     "uot_sinkhorn": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _D, _P, _SZ,
@@ -110,7 +111,7 @@ SIGNATURES = {
                                            ctypes.POINTER(UotBatchTuning), _P, _SZ, _P]),
     "uot_sinkhorn_batched": (ctypes.c_int, [_P, _P]),
     "uot_batched_results": (ctypes.c_int, [_P, _I32, ctypes.POINTER(UotResult), _P]),
-    "uot_batched_placement": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
+    "uot_batched_placement": (_I32, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "uot_fused_config": (_I32, [_I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                 ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
 }
@@ -210,6 +211,22 @@ def uot_selftest_wait(counter, target: int, complete: bool, limit_s: float, stat
     _check(load().uot_selftest_wait(counter.data_ptr(), int(target), 1 if complete else 0,
                                     float(limit_s), status.data_ptr(), _stream(stream)),
            "uot_selftest_wait")
+
+
+def uot_selftest_factor(target, total, fi: float, stream=None):
+    """The library's rescaling factor (target/total)^fi for float32 device
+    vectors; returns (factors, status bits)."""
+    torch = _torch()
+    n = target.numel()
+    t = target.contiguous()
+    s_ = total.contiguous()
+    if t.dtype != torch.float32 or s_.dtype != torch.float32 or s_.numel() != n or not t.is_cuda:
+        raise ValueError("target and total must be float32 CUDA vectors of one length")
+    out = torch.empty_like(t)
+    st = torch.zeros(1, dtype=torch.int32, device=t.device)
+    _check(load().uot_selftest_factor(t.data_ptr(), s_.data_ptr(), n, float(fi), out.data_ptr(),
+                                      st.data_ptr(), _stream(stream)), "uot_selftest_factor")
+    return out, int(st.item())
 
 
 def uot_fused_config(k: int):
@@ -454,13 +471,18 @@ def uot_sinkhorn_batched(ws, stream=None):
     _check(load().uot_sinkhorn_batched(ws.data_ptr(), _stream(stream)), "uot_sinkhorn_batched")
 
 
-def uot_batched_placement(ws, nprob: int) -> list:
-    """Per prepared problem: its on-chip cluster size, or 0 if it streams."""
+def uot_batched_placement(ws, nprob: int, teams: bool = False):
+    """Per prepared problem: its on-chip cluster size, or 0 if it streams;
+    with teams=True also the streaming team size class (0 on chip)."""
     out = (_I32 * nprob)()
-    k = load().uot_batched_placement(ws.data_ptr(), nprob, out)
+    team = (_I32 * nprob)()
+    k = load().uot_batched_placement(ws.data_ptr(), nprob, out, team)
     if k < 0:
         raise UotError(UOT_ERR_INVALID_ARG, "uot_batched_placement")
-    return list(out)[:min(k, nprob)]
+    k = min(k, nprob)
+    if teams:
+        return list(out)[:k], list(team)[:k]
+    return list(out)[:k]
 
 
 def uot_batched_results(ws, nprob: int, stream=None, check_status: bool = True):

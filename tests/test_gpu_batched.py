@@ -201,20 +201,40 @@ def test_autotune_picks_a_working_schedule(uot):
 @pytest.mark.slow
 def test_uneven_batch_full_size_sampled(uot):
     """512 problems, N and M log-uniform in [64, 4096], 200 iterations each,
-    in the launch configuration the benchmark uses (autotuned schedule); a
-    sample of problems is compared with the oracle."""
-    from paper_2412_11079_gb300.batch import Batch, autotune
+    in the launch configuration the benchmark times: the schedule the
+    autotuner picks from the benchmark's own candidates.  At least 32
+    problems are compared with the oracle: four from every decile of size,
+    and at least one of every on-chip cluster size and every streaming team
+    size class that the schedule uses."""
+    from paper_2412_11079_gb300.batch import Batch, autotune, candidates
     probs = workloads.batch_uneven(seed=0)
     B = Batch(probs)
-    autotune(B, [uot.batch_tuning(4, 32, 4e7), uot.batch_tuning(4, 64, 1e7)])
+    best, _ = autotune(B)
+    assert any((c.stages, c.max_team, c.target_elems, c.resident_max_cluster) ==
+               (best.stages, best.max_team, best.target_elems, best.resident_max_cluster)
+               for c in candidates())
     B.init_plans()
     B.run()
     res = B.results()
     assert all(r.iters_done == 200 and r.dev_status == 0 for r in res)
+    place, teams = B.placement(), B.teams()
     sizes = np.array([p.C.size for p in probs])
-    order = np.argsort(sizes)
-    sample = list(order[:3]) + list(order[len(order) // 2:len(order) // 2 + 2]) + [order[-60]]
-    for i in sample:
+    order = np.argsort(sizes, kind="stable")
+    sample = set()
+    for d in range(10):
+        chunk = order[d * len(order) // 10:(d + 1) * len(order) // 10]
+        sample.update(int(i) for i in chunk[[0, len(chunk) // 3, 2 * len(chunk) // 3, -1]])
+    for key in sorted(set(place) - {0}):
+        sample.add(next(i for i in order if place[i] == key))
+    for key in sorted(set(teams) - {0}):
+        sample.add(next(i for i in order[::-1] if teams[i] == key))
+    covered_clusters = {place[i] for i in sample} - {0}
+    covered_teams = {teams[i] for i in sample} - {0}
+    assert covered_clusters == set(place) - {0} and covered_teams == set(teams) - {0}
+    assert len(sample) >= 32 and any(place[i] for i in sample) and \
+        any(not place[i] for i in sample)
+    for i in sorted(sample):
         p = probs[i]
         ref = oracle.sinkhorn(oracle.init_plan(p.C, p.reg), p.a, p.b, p.reg, p.reg_m, p.iters)
-        assert rel_err(B.plans[i].double().cpu().numpy(), ref.plan) <= FP32_TOL, p.name
+        assert rel_err(B.plans[i].double().cpu().numpy(), ref.plan) <= FP32_TOL, \
+            (p.name, place[i], teams[i])
