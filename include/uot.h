@@ -95,6 +95,26 @@ typedef enum uot_rule { UOT_RULE_PAPER = 0, UOT_RULE_POT = 1 } uot_rule;
  *          iterations of the same plan).  Fused algorithm only. */
 typedef enum uot_storage { UOT_STORAGE_INPLACE = 0, UOT_STORAGE_KFORM = 1 } uot_storage;
 
+/* How uot_sinkhorn and uot_sinkhorn_kform launch the iterations.
+ * AUTO:       PERSISTENT when its conditions hold, else PASSES.
+ * PASSES:     one fused-pass launch per iteration (Algorithm 1's sweep with
+ *             the plan streamed from memory each time).
+ * PERSISTENT: one cooperative launch runs every iteration: each CTA (one per
+ *             SM) keeps a block of rows in shared memory for the whole solve,
+ *             adds its column partial sums into the workspace, and meets the
+ *             other CTAs at a bounded grid barrier once per iteration; the
+ *             rows go back to memory once, at the end.  For plans that fit in
+ *             the shared memory of the GPU's CTAs (about 220 KB per CTA: up to
+ *             about 30 MB of FP32 plan, e.g. N = M = 2048) where the per-pass
+ *             launch would dominate.  Needs the fused algorithm, no forced
+ *             tile or cluster, and no deterministic mode or adjoint history;
+ *             otherwise (or if the plan does not fit) UOT_ERR_UNSUPPORTED. */
+typedef enum uot_schedule {
+  UOT_SCHED_AUTO = 0,
+  UOT_SCHED_PASSES = 1,
+  UOT_SCHED_PERSISTENT = 2
+} uot_schedule;
+
 /* Bits of uot_result.dev_status. */
 #define UOT_DEV_ZERO_SUM 1u
 #define UOT_DEV_NONFINITE 2u
@@ -121,6 +141,7 @@ typedef struct uot_options {
                            dynamic row schedule).  Slower (static rows, one
                            more launch per iteration); one row per step.
                            uot_sinkhorn and uot_sinkhorn_kform only.        */
+  int32_t schedule;     /* uot_schedule (default UOT_SCHED_AUTO)              */
   int32_t reserved[1];  /* must be 0                                          */
   void* pass_events[2]; /* optional cudaEvent_t pair: uot_sinkhorn records
                            [0] on `stream` just before its first iteration

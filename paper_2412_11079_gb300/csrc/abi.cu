@@ -159,6 +159,7 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
   if (o.rule != UOT_RULE_PAPER && o.rule != UOT_RULE_POT) return UOT_ERR_INVALID_ARG;
   if (o.storage != UOT_STORAGE_INPLACE && o.storage != UOT_STORAGE_KFORM) return UOT_ERR_INVALID_ARG;
   if (o.deterministic != 0 && o.deterministic != 1) return UOT_ERR_INVALID_ARG;
+  if (o.schedule < UOT_SCHED_AUTO || o.schedule > UOT_SCHED_PERSISTENT) return UOT_ERR_INVALID_ARG;
   if (o.algo != UOT_ALGO_FUSED && o.algo != UOT_ALGO_MULTIPASS) return UOT_ERR_INVALID_ARG;
   const bool det = o.deterministic == 1;
   // uot_sinkhorn with kernel-form storage: the plan buffer is K (read-only
@@ -195,6 +196,20 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
   uint8_t* ws = static_cast<uint8_t*>(workspace);
   const int N = int(n), M = int(m);
 
+  // Persistent schedule (every iteration in one launch, rows held in shared
+  // memory) where the plan fits; decided before anything is enqueued.
+  PersistPlan pp{};
+  bool persist = false;
+  if (o.schedule != UOT_SCHED_PASSES && iters > 0) {
+    const bool eligible = o.algo == UOT_ALGO_FUSED && !det && !hist && o.tile == 0 &&
+                          o.cluster == 0;
+    if (eligible) {
+      if (persistent_plan(o.dtype, kfo, N, M, o.max_ctas, &pp) != cudaSuccess) return UOT_ERR_CUDA;
+      persist = pp.ok;
+    }
+    if (o.schedule == UOT_SCHED_PERSISTENT && !persist) return UOT_ERR_UNSUPPORTED;
+  }
+
   // Fused-pass geometry, validated before anything is enqueued.
   int k = -1, cs = 1, grid = 0, stages = 0, pair = -1;
   size_t smem = 0;
@@ -203,12 +218,12 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
   // Kernel form with bulk copies and no forced configuration: two rows per
   // step (kform_pair.cu); deterministic mode keeps the one-row pass.
   if (kfo && o.algo == UOT_ALGO_FUSED && iters > 0 && tma_ok && o.tile == 0 && o.cluster == 0 &&
-      !det)
+      !det && !persist)
     pair = kform_pair_pick(o.dtype, m, &cs);
   if (pair >= 0) {
     if (kform_pair_geometry(pair, cs, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
     if (o.max_ctas > 0 && grid > o.max_ctas) grid = std::max(cs, (o.max_ctas / cs) * cs);
-  } else if (o.algo == UOT_ALGO_FUSED && iters > 0) {
+  } else if (o.algo == UOT_ALGO_FUSED && iters > 0 && !persist) {
     k = fused_pick(o.dtype, m, o.tile);
     if (k < 0) return UOT_ERR_INVALID_ARG;
     FusedConfig cfg;
@@ -245,6 +260,16 @@ static uot_status run_sinkhorn(bool kf, void* mat, int64_t ldm, const float* a, 
     if (ev1 && cudaEventRecord(ev1, s) != cudaSuccess) return UOT_ERR_CUDA;
   } else if (iters == 0) {
     if (ev1 && cudaEventRecord(ev1, s) != cudaSuccess) return UOT_ERR_CUDA;
+  } else if (persist) {
+    float* Vws = reinterpret_cast<float*>(ws + L.beta);
+    if (persistent_launch(o.dtype, kfo, pp, mat, ldm, N, M, a, b, fi, iters, tol, o.check_every,
+                          ws, L, U, Vws, pot ? 1 : 0,
+                          std::ldexp(1.0f, int(std::lround(k_log2_scale))), !kf,
+                          s) != cudaSuccess)
+      return UOT_ERR_CUDA;
+    if (ev1 && cudaEventRecord(ev1, s) != cudaSuccess) return UOT_ERR_CUDA;
+    // The kernel form's entry point hands V back to the caller.
+    if (kf && launch_kform_finish(V, M, iters, ws, L, tol, s) != cudaSuccess) return UOT_ERR_CUDA;
   } else {
     const bool tma = reinterpret_cast<uintptr_t>(mat) % 16 == 0 &&
                      (uint64_t(ldm) * esize(o.dtype)) % 16 == 0;

@@ -214,6 +214,22 @@ cudaError_t kform_pair_geometry(int pair, int cs, int n, int* grid, int* stages,
 cudaError_t kform_pair_launch(int pair, int cs, int grid, size_t smem, const FusedArgs& args,
                               cudaStream_t s);
 
+// Persistent iteration (persistent.cu): every iteration in one cooperative
+// launch with each CTA's rows held in shared memory.  persistent_plan sets
+// ok = false when the plan does not fit (or cooperative launches are not
+// available).
+struct PersistPlan {
+  bool ok;
+  int grid, rows, ldm;
+  size_t smem;
+};
+cudaError_t persistent_plan(int dtype, bool kf, int n, int m, int max_ctas, PersistPlan* out);
+cudaError_t persistent_launch(int dtype, bool kf, const PersistPlan& pl, void* plan, int64_t ldp,
+                              int n, int m, const float* a, const float* b, float fi, int iters,
+                              double tol, int check_every, uint8_t* ws, const WsLayout& L,
+                              float* U, float* V, int pot, float kscale, bool write_plan,
+                              cudaStream_t s);
+
 void count_launch(int k = 1);
 
 }  // namespace uot

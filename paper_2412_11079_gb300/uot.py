@@ -29,6 +29,7 @@ UOT_F32, UOT_BF16, UOT_F16 = 0, 1, 2
 UOT_ALGO_FUSED, UOT_ALGO_MULTIPASS = 0, 1
 UOT_RULE_PAPER, UOT_RULE_POT = 0, 1
 UOT_STORAGE_INPLACE, UOT_STORAGE_KFORM = 0, 1
+UOT_SCHED_AUTO, UOT_SCHED_PASSES, UOT_SCHED_PERSISTENT = 0, 1, 2
 UOT_DEV_ZERO_SUM, UOT_DEV_NONFINITE, UOT_DEV_TIMEOUT = 1, 2, 4
 
 
@@ -37,7 +38,8 @@ class UotOptions(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("cluster", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
                 ("rule", ctypes.c_int32), ("storage", ctypes.c_int32),
-                ("deterministic", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
+                ("deterministic", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1),
                 ("pass_events", ctypes.c_void_p * 2)]
 
 
@@ -182,7 +184,7 @@ def _stream(stream):
 def options(dtype: int = UOT_F32, algo: int = UOT_ALGO_FUSED, check_every: int = 1,
             tile: int = 0, cluster: int = 0, max_ctas: int = 0,
             rule: int = UOT_RULE_PAPER, storage: int = UOT_STORAGE_INPLACE,
-            deterministic: bool = False) -> UotOptions:
+            deterministic: bool = False, schedule: int = UOT_SCHED_AUTO) -> UotOptions:
     o = UotOptions()
     load().uot_default_options(ctypes.byref(o))
     o.dtype, o.algo, o.check_every, o.tile, o.cluster = dtype, algo, check_every, tile, cluster
@@ -190,6 +192,7 @@ def options(dtype: int = UOT_F32, algo: int = UOT_ALGO_FUSED, check_every: int =
     o.rule = rule
     o.storage = storage
     o.deterministic = 1 if deterministic else 0
+    o.schedule = schedule
     return o
 
 

@@ -43,12 +43,13 @@ def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def kform_gpu(uot, p, dtype=torch.float32, log2_scale=0, iters=None, tol=0.0, ld=None, rule=0):
+def kform_gpu(uot, p, dtype=torch.float32, log2_scale=0, iters=None, tol=0.0, ld=None, rule=0,
+              schedule=0):
     n, m = p.C.shape
     C = dev(p.C)
     store = torch.zeros((n, ld or m), dtype=dtype, device="cuda")
     K = store[:, :m]
-    opt = uot.options(uot.dtype_code(dtype), rule=rule)
+    opt = uot.options(uot.dtype_code(dtype), rule=rule, schedule=schedule)
     uot.uot_init_kernel_scaled(C, K, p.reg, log2_scale, opt)
     U, V, res = uot.uot_sinkhorn_kform(K, dev(p.a), dev(p.b), p.reg, p.reg_m,
                                        p.iters if iters is None else iters, tol, log2_scale,
@@ -62,9 +63,10 @@ def kform_gpu(uot, p, dtype=torch.float32, log2_scale=0, iters=None, tol=0.0, ld
 
 @pytest.mark.parametrize("n,m", [(1, 1), (3, 5), (33, 31), (127, 1000), (1000, 1025),
                                  (257, 4099), (65, 16387), (40, 40000)])
-def test_fp32_kernel_form_matches_oracle(uot, n, m):
+@pytest.mark.parametrize("schedule", [1, 0], ids=["passes", "auto"])
+def test_fp32_kernel_form_matches_oracle(uot, n, m, schedule):
     p = workloads.uniform2d(seed=n * 31 + m, n=n, m=m, reg=0.1, reg_m=0.7, iters=15)
-    plan, cost, U, V, res = kform_gpu(uot, p)
+    plan, cost, U, V, res = kform_gpu(uot, p, schedule=schedule)
     ref = oracle.sinkhorn(oracle.init_plan(p.C, p.reg), p.a, p.b, p.reg, p.reg_m, p.iters,
                           record=True)
     Ur, Vr = oracle.kernel_form_scalings(ref)

@@ -44,14 +44,14 @@ def dev(x):
 
 
 def run_gpu(uot, p, iters=None, dtype=torch.float32, algo=0, tile=0, cluster=0, ld=None,
-            tol=0.0, check_every=1, P0=None):
+            tol=0.0, check_every=1, P0=None, schedule=0):
     iters = p.iters if iters is None else iters
     n, m = p.C.shape
     C = dev(p.C)
     ld = ld or m
     store = torch.zeros((n, ld), dtype=dtype, device="cuda")
     plan = store[:, :m]
-    opt = uot.options(uot.dtype_code(dtype), algo, check_every, tile, cluster)
+    opt = uot.options(uot.dtype_code(dtype), algo, check_every, tile, cluster, schedule=schedule)
     if P0 is None:
         uot.uot_init_kernel(C, plan, p.reg, opt)
     else:
@@ -86,10 +86,14 @@ SHAPES = [(1, 1), (1, 7), (7, 1), (3, 5), (31, 33), (33, 31), (127, 1000), (1000
 
 
 @pytest.mark.parametrize("n,m", SHAPES)
-@pytest.mark.parametrize("algo", [0, 1])
-def test_shapes_match_oracle(uot, n, m, algo):
+@pytest.mark.parametrize("algo,schedule", [(0, 1), (0, 0), (1, 0)],
+                         ids=["fused-passes", "fused-auto", "multipass"])
+def test_shapes_match_oracle(uot, n, m, algo, schedule):
+    """Fused one launch per iteration, fused with the automatic schedule
+    (one persistent launch wherever the plan fits in shared memory), and
+    the multi-pass baseline."""
     p = workloads.uniform2d(seed=n * 7919 + m, n=n, m=m, reg=0.1, reg_m=0.7, iters=15)
-    got, cost, res, _ = run_gpu(uot, p, algo=algo)
+    got, cost, res, _ = run_gpu(uot, p, algo=algo, schedule=schedule)
     ref, ref_cost = run_oracle(p)
     assert res.dev_status == ref.status == 0
     assert rel_err(got, ref.plan) <= FP32_TOL
@@ -139,11 +143,12 @@ def test_forced_cluster_too_small_is_rejected(uot):
 
 
 @pytest.mark.parametrize("check_every", [1, 3])
-def test_stopping_rule(uot, check_every):
+@pytest.mark.parametrize("schedule", [1, 2], ids=["passes", "persistent"])
+def test_stopping_rule(uot, check_every, schedule):
     p = workloads.uniform2d(seed=9, n=200, m=150, reg=0.3, reg_m=1.0, iters=3000)
     tol = 1e-6
     ref, _ = run_oracle(p, tol=tol, check_every=check_every)
-    got, _, res, _ = run_gpu(uot, p, tol=tol, check_every=check_every)
+    got, _, res, _ = run_gpu(uot, p, tol=tol, check_every=check_every, schedule=schedule)
     assert 2 <= ref.iters_done < 3000
     # FP32 row sums can move the stop by an iteration or two.
     assert abs(res.iters_done - ref.iters_done) <= 2 * check_every
@@ -273,8 +278,12 @@ def test_launch_count(uot):
     n, m = p.C.shape
     plan = dev(oracle.init_plan(p.C, p.reg).astype(np.float32))
     before = uot.uot_launch_count()
-    uot.uot_sinkhorn(plan, dev(p.a), dev(p.b), p.reg, p.reg_m, 9)
+    uot.uot_sinkhorn(plan, dev(p.a), dev(p.b), p.reg, p.reg_m, 9,
+                     opt=uot.options(schedule=uot.UOT_SCHED_PASSES))
     assert uot.uot_launch_count() - before == 9 + 2  # reset + 9 passes + finish
+    before = uot.uot_launch_count()
+    uot.uot_sinkhorn(plan, dev(p.a), dev(p.b), p.reg, p.reg_m, 9)
+    assert uot.uot_launch_count() - before == 2  # reset + one persistent launch
 
 
 @pytest.mark.slow
