@@ -499,6 +499,46 @@ def measure_grad(args, batch: int, n: int, iters: int, steps: int, warmup: int,
     return out
 
 
+def measure_small(args, n: int, iters: int, reps: int):
+    """Small workload: N=M=n, 2-D uniform points, reg 0.05, reg_m 1.0,
+    `iters` iterations, FP32 in place.  The plan (4 MiB at 1024^2) lives on
+    chip, so the per-pass launch dominates: one launch per iteration against
+    the persistent schedule (all iterations in one launch, rows held in
+    shared memory).  Whole solves timed with CUDA events (init excluded)."""
+    import torch
+
+    from paper_2412_11079_gb300 import uot, workloads
+
+    p = workloads.small_case(seed=0, n=n, m=n, iters=iters)
+    C = torch.from_numpy(p.C).cuda()
+    a = torch.from_numpy(p.a).cuda()
+    b = torch.from_numpy(p.b).cuda()
+    plan = torch.empty((n, n), device="cuda")
+    out = {"workload": f"small: N=M={n}, 2-D uniform points, reg 0.05, reg_m 1.0, "
+                       f"{iters} iterations, FP32 in place (plan held on chip)", "unit": UNIT}
+    for name, sched in (("per_pass_launches", uot.UOT_SCHED_PASSES),
+                        ("persistent", uot.UOT_SCHED_PERSISTENT)):
+        opt = uot.options(schedule=sched)
+        ws = uot.workspace(n, n, opt)
+        best = float("inf")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for rep in range(reps + 1):
+            uot.uot_init_kernel(C, plan, p.reg, opt)
+            e0.record()
+            uot.uot_sinkhorn(plan, a, b, p.reg, p.reg_m, iters, 0.0, ws, opt, sync=False)
+            e1.record()
+            torch.cuda.synchronize()
+            if rep:
+                best = min(best, e0.elapsed_time(e1))
+        res = uot.uot_read_result(ws, n, n, opt)
+        assert res.dev_status == 0 and res.iters_done == iters
+        out[name] = {"us_per_iter": best * 1e3 / iters,
+                     "value": float(n) * n * iters / (best * 1e-3)}
+    out["persistent_over_per_pass"] = (out["persistent"]["value"] /
+                                       out["per_pass_launches"]["value"])
+    return out
+
+
 def run_precision(args):
     import torch  # noqa: F401
 
@@ -847,11 +887,12 @@ def main():
             del dC, dplan, da, db, dcost
             torch.cuda.empty_cache()
             # The other workloads, bounded so the default run stays within a
-            # few minutes: reduced precision at N=M=32768 (accuracy at
-            # 8192^2), 512 uneven problems, and 32 problems forward +
-            # adjoint.  Each reports its own elements/s against the plain
+            # few minutes: the small on-chip problem (N=M=1024), reduced
+            # precision at N=M=32768 (accuracy at 8192^2), 512 uneven
+            # problems, and 32 problems forward + adjoint.  Each reports its own elements/s against the plain
             # FP32 path and the roofline of its dominant kernel.
             t0 = time.perf_counter()
+            compare["small_1024"] = measure_small(args, 1024, 100, 5)
             compare["precision_32768"] = measure_precision(args, 32768, 300, args.acc_n, 2)
             compare["batched_512"] = measure_batched(args, 512, 200, 3, 3, True)
             compare["grad_32x2048"] = measure_grad(args, 32, 2048, 200, 3, 3,

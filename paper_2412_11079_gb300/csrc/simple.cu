@@ -217,7 +217,8 @@ __global__ void kform_finish_kernel(float* V, const float* V_ws, int m, int iter
 }
 
 __global__ void reset_kernel(Control* ctl, double* err_ring, float* c1, int mpad, const float* b,
-                             float* b_ws, int m, int* ctr, float* beta) {
+                             float* b_ws, int m, int* ctr, float* beta, float* crep1,
+                             int crep_len) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g == 0) {
     ctl->status = 0;
@@ -233,6 +234,7 @@ __global__ void reset_kernel(Control* ctl, double* err_ring, float* c1, int mpad
     b_ws[j] = j < m ? b[j] : 0.0f;
     beta[j] = 0.0f;
   }
+  for (int j = g; j < crep_len; j += gridDim.x * blockDim.x) crep1[j] = 0.0f;
 }
 
 // ---- multi-pass iteration: 5 launches, 3 reads + 2 writes of the plan ----
@@ -492,12 +494,18 @@ cudaError_t launch_wait_selftest(const int* counter, int target, int complete, u
 
 cudaError_t launch_reset(uint8_t* ws, WsLayout L, const float* b, int m, cudaStream_t s) {
   const int blocks = int((L.mpad + TB - 1) / TB);
+  // Ring slot 1 of the persistent schedule's column-sum replicas (when the
+  // workspace has them) starts at zero too.
+  const int crep_len = L.mpad <= PERSIST_REP_MAX_M ? PERSIST_REPS * int(L.mpad) : 0;
   reset_kernel<<<blocks, TB, 0, s>>>(reinterpret_cast<Control*>(ws + L.ctl),
                                      reinterpret_cast<double*>(ws + L.err),
                                      reinterpret_cast<float*>(ws + L.c[1]), int(L.mpad), b,
                                      reinterpret_cast<float*>(ws + L.bws), m,
                                      reinterpret_cast<int*>(ws + L.ctr),
-                                     reinterpret_cast<float*>(ws + L.beta));
+                                     reinterpret_cast<float*>(ws + L.beta),
+                                     reinterpret_cast<float*>(ws + L.crep) +
+                                         size_t(PERSIST_REPS) * size_t(L.mpad),
+                                     crep_len);
   return last();
 }
 

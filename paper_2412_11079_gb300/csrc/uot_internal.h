@@ -32,6 +32,12 @@ struct Control {
 // column partial sums.
 constexpr int DET_SLOTS = 304;
 
+// Persistent schedule: CTAs add their column partials into one of this many
+// replicas of the column sums (fewer reductions meeting at one address),
+// for rows of at most PERSIST_REP_MAX_M columns.
+constexpr int PERSIST_REPS = 4;
+constexpr int64_t PERSIST_REP_MAX_M = 8192;
+
 // Offsets (bytes) of the workspace regions for an n x m problem.
 struct WsLayout {
   size_t ctl;     // Control
@@ -45,6 +51,8 @@ struct WsLayout {
   size_t beta;    // float[mpad]: column factors of the last completed pass
   size_t log2k;   // double: log2 of the fixed-point row factor (kernel-form gauge)
   size_t u;       // float[npad]: row scalings U of uot_sinkhorn's kernel-form storage
+  size_t crep;    // float[3][PERSIST_REPS][mpad] when mpad <= PERSIST_REP_MAX_M: the
+                  // persistent schedule's column sums, in replicas (else it uses c[3])
   size_t part;    // float[DET_SLOTS][mpad]: deterministic mode, column partials per slot
   size_t err_part;// double[DET_SLOTS][2]: deterministic mode, stopping-error partials
   size_t total;
@@ -69,6 +77,8 @@ inline WsLayout ws_layout(int64_t n, int64_t m, bool det = false) {
   L.beta = off; off = align256(off + size_t(L.mpad) * 4);
   L.log2k = off; off = align256(off + sizeof(double));
   L.u = off; off = align256(off + size_t(L.npad) * 4);
+  L.crep = off;
+  if (L.mpad <= PERSIST_REP_MAX_M) off = align256(off + size_t(3 * PERSIST_REPS) * size_t(L.mpad) * 4);
   L.part = off;
   if (det) off = align256(off + size_t(DET_SLOTS) * size_t(L.mpad) * 4);
   L.err_part = off;
