@@ -565,6 +565,75 @@ def run_grad(args):
                                   args.grad_check_iters)), flush=True)
 
 
+def run_shard_rows(args, world: int, rank: int, local: int):
+    """The large problem with its rows split over the ranks (Section 5.5):
+    each rank holds N/world rows and the column sums are all-reduced (NCCL,
+    on the device) between the sharded passes.  Strong scaling: the whole
+    job is one problem.  With one rank the reduction is the identity."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_11079_gb300 import build, shard, uot
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    uot.load()
+    p = make_problem(0, args)
+    n, m, iters = args.n, args.m, args.iters
+    lo, hi = rank * n // world, (rank + 1) * n // world
+    C = torch.from_numpy(np.ascontiguousarray(p.C[lo:hi])).to(dev)
+    a = torch.from_numpy(p.a[lo:hi].copy()).to(dev)
+    b = torch.from_numpy(p.b).to(dev)
+    plan = torch.empty((hi - lo, m), device=dev)
+    allreduce = (lambda t: dist.all_reduce(t)) if world > 1 else (lambda t: None)
+
+    def step():
+        uot.uot_init_kernel(C, plan, p.reg)
+        return shard.sinkhorn_rows(plan, a, b, p.reg, p.reg_m, iters, allreduce)
+
+    for _ in range(args.warmup):
+        assert step() == 0
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(bus_id_of(torch, dev)) if rank == 0 else None
+    launches0 = uot.uot_launch_count()
+    start.record()
+    for _ in range(args.steps):
+        step()
+    stop.record()
+    torch.cuda.synchronize()
+    launches = uot.uot_launch_count() - launches0
+    clocks = sampler.stop() if sampler else None
+    ms = start.elapsed_time(stop)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    value = float(n) * m * iters * args.steps / (ms * 1e-3)
+    if rank == 0:
+        cfg = config_of(args)
+        cfg.update({"algo": "fused one-pass, plan in place, rows sharded over the ranks "
+                            "(column sums all-reduced between passes)",
+                    "parallelism": f"rows/{world}"})
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": cfg, "gpu_launches": launches,
+            "clocks": clocks}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def config_of(args, reference: bool = False):
     c = {"workload": f"single UOT problem N=M={args.n}" if args.n == args.m else
          f"single UOT problem {args.n}x{args.m}",
@@ -607,6 +676,9 @@ def main():
     ap.add_argument("--grad-max-ctas", type=int, default=80)
     ap.add_argument("--grad-bwd-max-ctas", type=int, default=40)
     ap.add_argument("--acc-n", type=int, default=8192)
+    ap.add_argument("--shard", default="", choices=["", "rows"],
+                    help="rows: the large problem's rows split over the ranks, column sums "
+                         "all-reduced between passes (strong scaling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -616,6 +688,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.shard == "rows":
+        run_shard_rows(args, world, rank, local)
         return
     if args.workload == "grad":
         if args.n == 16384 and args.m == 16384:

@@ -403,6 +403,43 @@ uot_status uot_sinkhorn_noalloc(void* plan, int64_t ldp, const float* a, const f
                                 uot_result* out);
 
 /*
+ * Row-sharded iteration (Section 5.5: the rows are split over processes, and
+ * the one exchange per iteration is an all-reduce of the column-sum vector,
+ * which replaces the final reduction of Algorithm 1).  A process holds the
+ * rows [lo, hi) of the plan (n = hi - lo rows here, all m columns), their
+ * targets a[lo..hi), and all of b.  One iteration t = 1, 2, ...:
+ *   uot_shard_pass     the fused pass over the block: applies the column
+ *                      factors of iteration t-1 (beta_in, m device floats;
+ *                      NULL at t = 1: none pending), forms and applies the
+ *                      row factors (a_i / r_i)^fi, and writes the block's
+ *                      column sums of iteration t to colsum (m device floats,
+ *                      overwritten);
+ *   (caller)           all-reduces colsum (sum) over the processes;
+ *   uot_shard_factors  beta_j = (b_j / c_j)^fi from the reduced sums into
+ *                      beta (m device floats); degenerate-case bits are OR-ed
+ *                      into *status_dev when it is not NULL.
+ * After the last iteration uot_shard_finish multiplies column j of the block
+ * by beta_j, so the block holds its rows of the plan after the column step
+ * of the last iteration, as uot_sinkhorn would leave them.  With one process
+ * the sequence equals uot_sinkhorn's (in-place storage, fused passes).
+ * uot_shard_pass takes the workspace of uot_sinkhorn for an n x m problem; t
+ * only sets the direction in which the pass visits the rows.  Options: FP32,
+ * BF16 or FP16 plans, the rule of Section 2.1, in-place storage and fused
+ * passes only (UOT_ERR_UNSUPPORTED otherwise); no stopping rule (the caller
+ * decides after the reduction).  The row factors' degenerate-case bits
+ * accumulate in the workspace from the first pass (beta_in NULL) on:
+ * uot_read_result reports them.  All three are asynchronous.
+ */
+uot_status uot_shard_pass(void* plan, int64_t ldp, const float* a, int64_t n, int64_t m,
+                          float reg, float reg_m, int32_t t, const float* beta_in, float* colsum,
+                          void* workspace, size_t ws_bytes, const uot_options* opt,
+                          void* stream);
+uot_status uot_shard_factors(const float* colsum, const float* b, int64_t m, float reg,
+                             float reg_m, float* beta, uint32_t* status_dev, void* stream);
+uot_status uot_shard_finish(void* plan, int64_t ldp, int64_t n, int64_t m, int32_t dtype,
+                            const float* beta, void* stream);
+
+/*
  * Batched iteration: many independent problems of uneven size (Section 2.1
  * rule, one sweep per iteration as in Algorithm 1; FP32 plans, overwritten
  * by the result).  Two engines share a batch:

@@ -381,6 +381,104 @@ uot_status uot_sinkhorn_kform_save(const void* K, int64_t ldk, const float* a, c
                       k_log2_scale, U, V, workspace, ws_bytes, opt, stream, out, hist, hist_bytes);
 }
 
+uot_status uot_shard_pass(void* plan, int64_t ldp, const float* a, int64_t n, int64_t m,
+                          float reg, float reg_m, int32_t t, const float* beta_in, float* colsum,
+                          void* workspace, size_t ws_bytes, const uot_options* opt,
+                          void* stream) {
+  const uot_options o = resolve(opt);
+  if (!plan || !a || !colsum || !valid_dims(n, m) || ldp < m || !valid_dtype(o.dtype) || t < 1)
+    return UOT_ERR_INVALID_ARG;
+  if (!(reg > 0.0f) || !std::isfinite(reg) || !(reg_m > 0.0f) || !reserved_zero(o))
+    return UOT_ERR_INVALID_ARG;
+  if (o.algo != UOT_ALGO_FUSED || o.storage != UOT_STORAGE_INPLACE || o.deterministic ||
+      o.rule != UOT_RULE_PAPER || o.schedule == UOT_SCHED_PERSISTENT)
+    return UOT_ERR_UNSUPPORTED;
+  if (o.cluster < 0 || o.cluster > 8 || o.tile < 0 || o.max_ctas < 0) return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(plan) % esize(o.dtype) || reinterpret_cast<uintptr_t>(a) % 4 ||
+      reinterpret_cast<uintptr_t>(colsum) % 4 || reinterpret_cast<uintptr_t>(beta_in) % 4)
+    return UOT_ERR_INVALID_ARG;
+  const WsLayout L = ws_layout(n, m);
+  if (!workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(workspace) % 256)
+    return UOT_ERR_WORKSPACE;
+  const int N = int(n), M = int(m);
+  const int k = fused_pick(o.dtype, m, o.tile);
+  if (k < 0) return UOT_ERR_INVALID_ARG;
+  FusedConfig cfg;
+  fused_config_info(k, &cfg);
+  const int cs = o.cluster > 0 ? o.cluster : int((m + cfg.cols - 1) / cfg.cols);
+  if (cs > 8) return UOT_ERR_UNSUPPORTED;
+  if (int64_t(cs) * cfg.cols < m) return UOT_ERR_INVALID_ARG;
+  int grid = 0, stages = 0;
+  size_t smem = 0;
+  if (fused_geometry(false, k, cs, N, &grid, &stages, &smem) != cudaSuccess) return UOT_ERR_CUDA;
+  if (o.max_ctas > 0 && grid > o.max_ctas) grid = std::max(cs, (o.max_ctas / cs) * cs);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  const double fi_d = std::isinf(reg_m) ? 1.0 : double(reg_m) / (double(reg_m) + double(reg));
+  if (launch_shard_prep(ws, L, beta_in, M, s) != cudaSuccess) return UOT_ERR_CUDA;
+  FusedArgs A{};
+  A.plan = plan;
+  A.ldp = ldp;
+  A.n = N;
+  A.m = M;
+  A.a = a;
+  A.fi = float(fi_d);
+  A.t = t;
+  A.first = beta_in ? 0 : 1;
+  A.mpad = int(L.mpad);
+  A.c_prev = reinterpret_cast<float*>(ws + L.c[0]);
+  A.c_next = reinterpret_cast<float*>(ws + L.c[0]);
+  A.c_clear = reinterpret_cast<float*>(ws + L.c[1]);
+  A.r_prev = reinterpret_cast<float*>(ws + L.r);
+  A.ctl = reinterpret_cast<Control*>(ws + L.ctl);
+  A.stages = stages;
+  A.b_ws = reinterpret_cast<const float*>(ws + L.bws);
+  int* ctr = reinterpret_cast<int*>(ws + L.ctr);
+  A.row_ctr = ctr;
+  A.ctr_clear = ctr + 1;
+  A.arrive = ctr + 3;
+  A.arrive_clear = ctr + 4;
+  A.slice_ctr = ctr + 6;
+  A.slice_clear = ctr + 7;
+  A.dynamic = 1;
+  A.beta = reinterpret_cast<const float*>(ws + L.beta);
+  A.beta_out = reinterpret_cast<float*>(ws + L.beta);
+  A.no_factors = 1;
+  const bool tma = reinterpret_cast<uintptr_t>(plan) % 16 == 0 &&
+                   (uint64_t(ldp) * esize(o.dtype)) % 16 == 0;
+  if (fused_launch(false, k, cs, grid, smem, tma, A, s) != cudaSuccess) return UOT_ERR_CUDA;
+  if (cudaMemcpyAsync(colsum, ws + L.c[0], size_t(M) * 4, cudaMemcpyDeviceToDevice, s) !=
+      cudaSuccess)
+    return UOT_ERR_CUDA;
+  return UOT_OK;
+}
+
+uot_status uot_shard_factors(const float* colsum, const float* b, int64_t m, float reg,
+                             float reg_m, float* beta, uint32_t* status_dev, void* stream) {
+  if (!colsum || !b || !beta || !valid_dims(1, m)) return UOT_ERR_INVALID_ARG;
+  if (!(reg > 0.0f) || !std::isfinite(reg) || !(reg_m > 0.0f)) return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(colsum) % 4 || reinterpret_cast<uintptr_t>(b) % 4 ||
+      reinterpret_cast<uintptr_t>(beta) % 4 || reinterpret_cast<uintptr_t>(status_dev) % 4)
+    return UOT_ERR_INVALID_ARG;
+  const double fi_d = std::isinf(reg_m) ? 1.0 : double(reg_m) / (double(reg_m) + double(reg));
+  return launch_shard_factors(colsum, b, int(m), float(fi_d), beta, status_dev,
+                              static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? UOT_OK
+             : UOT_ERR_CUDA;
+}
+
+uot_status uot_shard_finish(void* plan, int64_t ldp, int64_t n, int64_t m, int32_t dtype,
+                            const float* beta, void* stream) {
+  if (!plan || !beta || !valid_dims(n, m) || ldp < m || !valid_dtype(dtype))
+    return UOT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(plan) % esize(dtype) || reinterpret_cast<uintptr_t>(beta) % 4)
+    return UOT_ERR_INVALID_ARG;
+  return launch_scale_cols(plan, ldp, int(n), int(m), dtype, beta,
+                           static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? UOT_OK
+             : UOT_ERR_CUDA;
+}
+
 uot_status uot_init_kernel_scaled(const float* C, int64_t ldc, void* K, int64_t ldk, int64_t n,
                                   int64_t m, float reg, float log2_scale, const uot_options* opt,
                                   void* stream) {

@@ -449,8 +449,9 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_kernel(const FusedArgs 
   // beta_t = (b_j / c_j)^fi for the next pass (kernel form: V <- V beta_t),
   // computed once per column by the CTAs that finish last, in slices, after
   // every CTA's column partials have landed (deterministic mode: by the
-  // reduction launch that follows the pass).
-  if (!p.det) {
+  // reduction launch that follows the pass; a row-sharded pass leaves the
+  // column sums to be reduced across processes first).
+  if (!p.det && !p.no_factors) {
     const int nsl = BETA_SLICES;
     const int per = (m + nsl - 1) / nsl;
     uint32_t st2 = 0;

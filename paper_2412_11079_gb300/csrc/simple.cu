@@ -486,6 +486,72 @@ cudaError_t launch_factor_selftest(const float* target, const float* total, int6
   return last();
 }
 
+// Row-sharded pass set-up: the previous column factors into the zero-padded
+// factor buffer (ones when there are none yet, and then the status word is
+// cleared too: a new solve), the column sums of this pass and the pass
+// counters cleared.
+__global__ void shard_prep_kernel(const float* beta_in, int m, int mpad, float* beta_ws,
+                                  float* c_next, int* ctr, Control* ctl) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gs = gridDim.x * blockDim.x;
+  if (g == 0 && !beta_in) {
+    ctl->status = 0;
+    ctl->done = 0;
+  }
+  for (int j = g; j < mpad; j += gs) {
+    beta_ws[j] = j < m ? (beta_in ? beta_in[j] : 1.0f) : 0.0f;
+    c_next[j] = 0.0f;
+  }
+  if (g < 9) ctr[g] = 0;
+}
+
+// beta_j = (b_j / c_j)^fi from the reduced column sums.
+__global__ void shard_factors_kernel(const float* c, const float* b, int m, float fi, float* beta,
+                                     uint32_t* status) {
+  uint32_t st = 0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x)
+    beta[j] = rescale_factor(b[j], c[j], fi, st);
+  if (st && status) atomicOr(status, st);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TB) scale_cols_kernel(T* P, int64_t ldp, int n, int m,
+                                                        const float* __restrict__ beta) {
+  const int j = blockIdx.x * TB + threadIdx.x;
+  if (j >= m) return;
+  const float g = beta[j];
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    T* q = P + int64_t(i) * ldp + j;
+    Elem<T>::store1(q, Elem<T>::load1(q) * g);
+  }
+}
+
+cudaError_t launch_shard_prep(uint8_t* ws, WsLayout L, const float* beta_in, int m, cudaStream_t s) {
+  const int blocks = int((L.mpad + TB - 1) / TB);
+  shard_prep_kernel<<<blocks, TB, 0, s>>>(beta_in, m, int(L.mpad),
+                                          reinterpret_cast<float*>(ws + L.beta),
+                                          reinterpret_cast<float*>(ws + L.c[0]),
+                                          reinterpret_cast<int*>(ws + L.ctr),
+                                          reinterpret_cast<Control*>(ws + L.ctl));
+  return last();
+}
+
+cudaError_t launch_shard_factors(const float* c, const float* b, int m, float fi, float* beta,
+                                 uint32_t* status, cudaStream_t s) {
+  const int blocks = std::min((m + TB - 1) / TB, sm_count() * 8);
+  shard_factors_kernel<<<blocks, TB, 0, s>>>(c, b, m, fi, beta, status);
+  return last();
+}
+
+cudaError_t launch_scale_cols(void* P, int64_t ldp, int n, int m, int dtype, const float* beta,
+                              cudaStream_t s) {
+  return by_dtype(dtype, [&](auto z) {
+    using T = decltype(z);
+    scale_cols_kernel<T><<<col_grid(n, m), TB, 0, s>>>(reinterpret_cast<T*>(P), ldp, n, m, beta);
+    return last();
+  });
+}
+
 cudaError_t launch_wait_selftest(const int* counter, int target, int complete, uint64_t limit_ns,
                                  uint32_t* status, cudaStream_t s) {
   wait_selftest_kernel<<<1, 32, 0, s>>>(counter, target, complete, limit_ns, status);

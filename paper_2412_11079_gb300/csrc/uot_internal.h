@@ -129,6 +129,8 @@ struct FusedArgs {
   int pot;             // kernel form: scaling-vector rule (uot_rule POT)
   float kscale;        // kernel form: storage scale of K (2^s; FP16 K is stored x 2^15)
   int det;             // 1: deterministic mode (static rows, partials to slots)
+  int no_factors;      // 1: leave the column sums in c_next, skip the end-of-pass job
+                       //    (row-sharded passes: the sums are reduced across processes)
   float* part;         // deterministic: column partials, slot g at part + g * mpad
   double* err_part;    // deterministic: stopping-error partials, slot g at 2 * g
 };
@@ -204,6 +206,14 @@ cudaError_t launch_finish(void* P, int64_t ldp, int n, int m, int dtype, const f
                           int check_every, bool beta_ready, cudaStream_t s);
 cudaError_t launch_cost(const void* P, int64_t ldp, const float* C, int64_t ldc, int n, int m,
                         int dtype, double* out, cudaStream_t s);
+// Row-sharded passes: workspace set-up of one pass (beta_in copied into the
+// zero-padded factor buffer, or ones when NULL; column sums and counters
+// cleared), the column factors from reduced sums, and the last column scale.
+cudaError_t launch_shard_prep(uint8_t* ws, WsLayout L, const float* beta_in, int m, cudaStream_t s);
+cudaError_t launch_shard_factors(const float* c, const float* b, int m, float fi, float* beta,
+                                 uint32_t* status, cudaStream_t s);
+cudaError_t launch_scale_cols(void* P, int64_t ldp, int n, int m, int dtype, const float* beta,
+                              cudaStream_t s);
 cudaError_t launch_reset(uint8_t* ws, WsLayout L, const float* b, int m, cudaStream_t s);
 cudaError_t launch_factor_selftest(const float* target, const float* total, int64_t count,
                                    float fi, float* out, uint32_t* status, cudaStream_t s);

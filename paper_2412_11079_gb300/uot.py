@@ -105,6 +105,10 @@ SIGNATURES = {
     "uot_sinkhorn_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _D,
                                             ctypes.POINTER(UotOptions), _P,
                                             ctypes.POINTER(UotResult)]),
+    "uot_shard_pass": (ctypes.c_int, [_P, _I64, _P, _I64, _I64, _F, _F, _I32, _P, _P, _P, _SZ,
+                                      ctypes.POINTER(UotOptions), _P]),
+    "uot_shard_factors": (ctypes.c_int, [_P, _P, _I64, _F, _F, _P, _P, _P]),
+    "uot_shard_finish": (ctypes.c_int, [_P, _I64, _I64, _I64, _I32, _P, _P]),
     "uot_batch_default_tuning": (None, [ctypes.POINTER(UotBatchTuning)]),
     "uot_batched_workspace_size": (_SZ, [ctypes.POINTER(UotProblem), _I32,
                                          ctypes.POINTER(UotOptions)]),
@@ -440,6 +444,39 @@ def solve(C, a, b, reg: float, reg_m: float = math.inf, iters: int = 100, tol: f
     res = uot_sinkhorn(plan, a, b, reg, reg_m, iters, tol, opt=opt, stream=stream)
     cost = uot_cost(plan, C, stream=stream)
     return plan, cost, res
+
+
+def uot_shard_pass(plan, a, reg: float, reg_m: float, t: int, beta_in, colsum, ws=None,
+                   opt: UotOptions | None = None, stream=None):
+    """One fused pass over a row block (rows of `plan`, targets `a`): applies
+    beta_in (None at t = 1), writes the block's column sums to `colsum`."""
+    n, m = plan.shape
+    opt = opt or options(dtype_code(plan.dtype))
+    if ws is None:
+        ws = workspace(n, m, opt, plan.device)
+    pp, ldp = _matrix(plan, "plan")
+    bp = None if beta_in is None else _vector(beta_in, "beta_in", m)
+    _check(load().uot_shard_pass(pp, ldp, _vector(a, "a", n), n, m, float(reg), float(reg_m),
+                                 int(t), bp, _vector(colsum, "colsum", m), ws.data_ptr(),
+                                 ws.numel(), ctypes.byref(opt), _stream(stream)),
+           "uot_shard_pass")
+    return ws
+
+
+def uot_shard_factors(colsum, b, reg: float, reg_m: float, beta, status=None, stream=None):
+    m = b.numel()
+    sp = None if status is None else status.data_ptr()
+    _check(load().uot_shard_factors(_vector(colsum, "colsum", m), _vector(b, "b", m), m,
+                                    float(reg), float(reg_m), _vector(beta, "beta", m), sp,
+                                    _stream(stream)), "uot_shard_factors")
+
+
+def uot_shard_finish(plan, beta, stream=None):
+    n, m = plan.shape
+    pp, ldp = _matrix(plan, "plan")
+    _check(load().uot_shard_finish(pp, ldp, n, m, dtype_code(plan.dtype),
+                                   _vector(beta, "beta", m), _stream(stream)),
+           "uot_shard_finish")
 
 
 def batch_tuning(stages: int | None = None, max_team: int | None = None,
