@@ -234,20 +234,23 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
       xa[k] = load_raw(sbase, ra, k);
       xb[k] = lb ? load_raw(sbase + rowb_off, rb, k) : make_uint4(0u, 0u, 0u, 0u);
     }
-    float sa = 0.0f, sb = 0.0f;
+    // Row sums of K V: even and odd columns in the two lanes of a packed
+    // FMA, added at the end.
+    float2 pa = make_float2(0.0f, 0.0f), pb = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
       float fa[VE], fb[VE];
       E::unpack(xa[k], fa);
       E::unpack(xb[k], fb);
 #pragma unroll
-      for (int e = 0; e < VE; ++e) {
-        sa = fmaf(fa[e], V[k][e], sa);
-        sb = fmaf(fb[e], V[k][e], sb);
+      for (int e = 0; e < VE; e += 2) {
+        const float2 v2 = make_float2(V[k][e], V[k][e + 1]);
+        pa = ffma2(make_float2(fa[e], fa[e + 1]), v2, pa);
+        pb = ffma2(make_float2(fb[e], fb[e + 1]), v2, pb);
       }
     }
-    sa = warp_sum(sa);
-    sb = warp_sum(sb);
+    float sa = warp_sum(pa.x + pa.y);
+    float sb = warp_sum(pb.x + pb.y);
     float* rq = red + (q & 1) * RQ;
     if (lane == 0) {
       if constexpr (!CL) {
@@ -329,8 +332,14 @@ __global__ void __launch_bounds__(THREADS, 1) kform_pair_kernel(const FusedArgs 
         E::unpack(load_raw(sbase, ra, k), fa);
         E::unpack(lb ? load_raw(sbase + rowb_off, rb, k) : make_uint4(0u, 0u, 0u, 0u), fb);
       }
+      const float2 ua2 = make_float2(ua, ua), ub2 = make_float2(ub, ub);
 #pragma unroll
-      for (int e = 0; e < VE; ++e) cacc[k][e] = fmaf(ub, fb[e], fmaf(ua, fa[e], cacc[k][e]));
+      for (int e = 0; e < VE; e += 2) {
+        float2 c2 = make_float2(cacc[k][e], cacc[k][e + 1]);
+        c2 = ffma2(ub2, make_float2(fb[e], fb[e + 1]), ffma2(ua2, make_float2(fa[e], fa[e + 1]), c2));
+        cacc[k][e] = c2.x;
+        cacc[k][e + 1] = c2.y;
+      }
     }
     ++done_steps;
   }
