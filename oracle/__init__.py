@@ -32,5 +32,6 @@ from .uot import (  # noqa: F401
     transport_cost,
     sinkhorn_grad,
     sinkhorn_grad_magnitude,
+    sinkhorn_tensor3,
     kernel_form_scalings,
 )

@@ -332,3 +332,23 @@ def sinkhorn_grad_magnitude(C, a, b, reg: float, reg_m: float, iters: int):
         dl += R * z[:, None]
         F = (1.0 - fi) * F
     return P + dl / reg, da, db
+
+
+def sinkhorn_tensor3(P0, a, b, c, reg: float, reg_m: float, iters: int) -> np.ndarray:
+    """The rule of Section 2.1 on a three-way plan (the paper notes the method
+    applies to higher-dimensional tensors; this is the reading used): every
+    iteration rescales along mode 1, then mode 2, then mode 3, each time by
+    ``(target / marginal sum)^fi`` with the degenerate readings of
+    ``scaling_factor``.  ``P0`` is n1 x n2 x n3; ``a``, ``b``, ``c`` are the
+    mode targets.  Returns the plan after the mode-3 step of the last
+    iteration (FP64)."""
+    fi = fi_exponent(reg, reg_m)
+    P = np.array(P0, dtype=np.float64, copy=True)
+    for _ in range(iters):
+        f1, _ = scaling_factor(a, P.sum(axis=(1, 2)), fi)
+        P *= f1[:, None, None]
+        f2, _ = scaling_factor(b, P.sum(axis=(0, 2)), fi)
+        P *= f2[None, :, None]
+        f3, _ = scaling_factor(c, P.sum(axis=(0, 1)), fi)
+        P *= f3[None, None, :]
+    return P

@@ -375,3 +375,63 @@ def test_pot_rule_zero_target_and_stopping():
     res = oracle.sinkhorn_pot(oracle.init_plan(C, 0.3), a, b, 0.3, 1.0, 200, tol=1e-9)
     assert np.all(res.plan[2] == 0.0) and res.status == 0
     assert res.iters_done < 200 and res.err <= 1e-9
+
+
+# --- the three-way (multi-marginal) form ------------------------------------
+
+
+def test_tensor3_single_entry_closed_form():
+    """1x1x1: with x = log P the iteration is x <- (1-fi) x + fi log a, then
+    with log b, then with log c."""
+    reg, reg_m, T = 0.4, 1.3, 9
+    fi = oracle.fi_exponent(reg, reg_m)
+    a, b, c = 0.7, 2.2, 0.35
+    x = -0.9 / reg
+    for _ in range(T):
+        for t in (a, b, c):
+            x = (1 - fi) * x + fi * math.log(t)
+    got = oracle.sinkhorn_tensor3(np.exp(np.array([[[-0.9 / reg]]])), [a], [b], [c], reg, reg_m,
+                                  T)
+    assert got[0, 0, 0] == pytest.approx(math.exp(x), rel=1e-13)
+
+
+def test_tensor3_with_one_mode_of_size_one_is_the_matrix_rule():
+    """n3 = 1, fi = 1 and c = sum(b): after the mode-2 (column) step the total
+    mass is sum(b), so the mode-3 factor is exactly 1 and the three-way rule
+    is textbook Sinkhorn on the n1 x n2 matrix."""
+    C, a, b = rand_problem(21, 9, 7)
+    reg, T = 0.3, 25
+    P0 = oracle.init_plan(C, reg)
+    got = oracle.sinkhorn_tensor3(P0[:, :, None], a, b, [b.sum()], reg, math.inf, T)[:, :, 0]
+    ref = oracle.sinkhorn(P0, a, b, reg, math.inf, T).plan
+    np.testing.assert_allclose(got, ref, rtol=1e-12)
+
+
+def test_tensor3_rank_one_cost_decouples():
+    """C_ijk = p_i + q_j + r_k: the plan stays an outer product x (x) y (x) z,
+    and each mode step rescales one vector by (target / (vector * product of
+    the other two totals))^fi -- three vector recurrences written out here."""
+    rng = np.random.default_rng(5)
+    p, q, r = rng.random(4), rng.random(3), rng.random(5)
+    C = p[:, None, None] + q[None, :, None] + r[None, None, :]
+    a, b, c = rng.uniform(0.5, 1.5, 4), rng.uniform(0.5, 1.5, 3), rng.uniform(0.5, 1.5, 5)
+    reg, reg_m, T = 0.5, 0.8, 12
+    fi = oracle.fi_exponent(reg, reg_m)
+    got = oracle.sinkhorn_tensor3(np.exp(-C / reg), a, b, c, reg, reg_m, T)
+    x, y, z = np.exp(-p / reg), np.exp(-q / reg), np.exp(-r / reg)
+    for _ in range(T):
+        x = x * (a / (x * y.sum() * z.sum())) ** fi
+        y = y * (b / (y * x.sum() * z.sum())) ** fi
+        z = z * (c / (z * x.sum() * y.sum())) ** fi
+    np.testing.assert_allclose(got, x[:, None, None] * y[None, :, None] * z[None, None, :],
+                               rtol=1e-12)
+
+
+def test_tensor3_mode_marginal_after_each_step():
+    """Per-step identity: after the last (mode-3) step the mode-3 sums are
+    c^fi s^(1-fi), s the sums before it; with fi = 1 they equal c."""
+    rng = np.random.default_rng(6)
+    P0 = rng.random((5, 4, 6))
+    a, b, c = rng.random(5), rng.random(4), rng.random(6) + 0.5
+    got = oracle.sinkhorn_tensor3(P0, a, b, c, 0.2, math.inf, 3)
+    np.testing.assert_allclose(got.sum(axis=(0, 1)), c, rtol=1e-12)
