@@ -539,6 +539,47 @@ def measure_small(args, n: int, iters: int, reps: int):
     return out
 
 
+def measure_tensor(args, n1: int, n: int, iters: int, reps: int):
+    """Three-way workload: n1 x n x n FP32 plan (2048 x 256 x 256 = 512 MiB,
+    larger than L2; a slice of n^2 entries is one row of the fused pass),
+    three uniform 2-D point clouds, C = sum of the pairwise squared
+    distances, reg 0.1, reg_m 1.0, `iters` iterations; one sweep of the plan
+    per iteration plus two small launches forming the mode-2 and mode-3
+    factors.  Roofline: one read and one write of the plan per iteration over
+    the event-timed iterations (the small launches included)."""
+    import torch
+
+    from paper_2412_11079_gb300 import uot, workloads
+
+    dev = torch.device("cuda", 0)
+    peak, peak_kind = measured_peaks()
+    C, a, b, c, reg, reg_m = workloads.tensor3_device(0, n1, n, n, dev)
+    P = torch.empty((n1, n, n), device=dev)
+    opt = uot.options()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(); e1.record()
+    opt.pass_events[0] = e0.cuda_event
+    opt.pass_events[1] = e1.cuda_event
+    ws = uot.workspace_bytes(int(uot.load().uot_tensor3_workspace_size(n1, n, n)), dev)
+    best = float("inf")
+    for rep in range(reps + 1):
+        uot.uot_init_kernel(C.view(n1, n * n), P.view(n1, n * n), reg)
+        res = uot.uot_sinkhorn_tensor3(P, a, b, c, reg, reg_m, iters, ws, opt)
+        assert res.dev_status == 0 and res.iters_done == iters
+        if rep:
+            best = min(best, e0.elapsed_time(e1) / iters)
+    elems = float(n1) * n * n
+    out = {"workload": f"three-way: {n1}x{n}x{n} FP32 plan, 2-D uniform points, C = sum of pairwise "
+                       f"squared distances, reg 0.1, reg_m 1.0, {iters} iterations", "unit": UNIT,
+           "ms_per_iter": best, "value": elems / (best * 1e-3),
+           "roofline": roofline_of("fused_pass_kernel<float,512,8> over the mode-1 unfolding "
+                                   "+ mode-2/3 factor launches", 8.0 * elems, best * 1e-3, peak,
+                                   peak_kind)}
+    del C, P
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_precision(args):
     import torch  # noqa: F401
 
@@ -968,6 +1009,7 @@ def main():
             # FP32 path and the roofline of its dominant kernel.
             t0 = time.perf_counter()
             compare["small_1024"] = measure_small(args, 1024, 100, 5)
+            compare["tensor3_2048x256x256"] = measure_tensor(args, 2048, 256, 100, 2)
             compare["precision_32768"] = measure_precision(args, 32768, 300, args.acc_n, 2)
             compare["batched_512"] = measure_batched(args, 512, 200, 3, 3, True)
             compare["grad_32x2048"] = measure_grad(args, 32, 2048, 200, 3, 3,

@@ -440,6 +440,37 @@ uot_status uot_shard_finish(void* plan, int64_t ldp, int64_t n, int64_t m, int32
                             const float* beta, void* stream);
 
 /*
+ * Three-way form.  The paper notes that the method applies to higher-
+ * dimensional tensors; this is the rule of Section 2.1 on a plan of
+ * n1 x n2 x n3 entries with mode targets a (n1), b (n2), c (n3): every
+ * iteration rescales along mode 1, then mode 2, then mode 3 by
+ * (target / marginal sum)^fi (degenerate readings as in uot_sinkhorn).  One
+ * sweep of the plan per iteration, as Algorithm 1 does for the matrix: a
+ * slice P[i, :, :] is a row of the mode-1 unfolding (n1 x n2 n3), so the
+ * fused pass applies the pending mode-2 and mode-3 factors, forms the slice
+ * factor and accumulates M_jk = sum_i of the rescaled slices; the mode-2
+ * factors come from the sums over k of M, the mode-3 factors from the sums
+ * over j of M weighted by the new mode-2 factors.
+ *   P          device, contiguous n1 x n2 x n3 (k fastest), FP32/BF16/FP16
+ *              (opt->dtype), in/out: P0 in, the plan after the mode-3 step
+ *              of the last iteration out.
+ *   a, b, c    device FP32 targets, read-only.
+ *   workspace  >= uot_tensor3_workspace_size(n1, n2, n3) bytes, 256-byte
+ *              aligned, caller-owned (0 on bad sizes: each >= 1, n2 n3 <= 2^30).
+ *   out        as in uot_sinkhorn (NULL: asynchronous).
+ * A slice is one row of the fused pass, split over at most a cluster of 8
+ * CTAs: n2 n3 <= 8 x 16384 = 131072 (wider slices: UOT_ERR_UNSUPPORTED).
+ * Options: fused passes, in-place storage, the rule of Section 2.1, no
+ * deterministic mode, no persistent schedule (UOT_ERR_UNSUPPORTED
+ * otherwise); no stopping rule.  Errors as uot_sinkhorn.
+ */
+size_t uot_tensor3_workspace_size(int64_t n1, int64_t n2, int64_t n3);
+uot_status uot_sinkhorn_tensor3(void* P, int64_t n1, int64_t n2, int64_t n3, const float* a,
+                                const float* b, const float* c, float reg, float reg_m,
+                                int32_t iters, void* workspace, size_t ws_bytes,
+                                const uot_options* opt, void* stream, uot_result* out);
+
+/*
  * Batched iteration: many independent problems of uneven size (Section 2.1
  * rule, one sweep per iteration as in Algorithm 1; FP32 plans, overwritten
  * by the result).  Two engines share a batch:

@@ -231,7 +231,7 @@ __global__ void reset_kernel(Control* ctl, double* err_ring, float* c1, int mpad
   if (g < 9) ctr[g] = 0;
   for (int j = g; j < mpad; j += gridDim.x * blockDim.x) {
     c1[j] = 0.0f;
-    b_ws[j] = j < m ? b[j] : 0.0f;
+    b_ws[j] = (b && j < m) ? b[j] : 0.0f;  // no b: a pass that forms no column factors
     beta[j] = 0.0f;
   }
   for (int j = g; j < crep_len; j += gridDim.x * blockDim.x) crep1[j] = 0.0f;

@@ -109,6 +109,10 @@ SIGNATURES = {
                                       ctypes.POINTER(UotOptions), _P]),
     "uot_shard_factors": (ctypes.c_int, [_P, _P, _I64, _F, _F, _P, _P, _P]),
     "uot_shard_finish": (ctypes.c_int, [_P, _I64, _I64, _I64, _I32, _P, _P]),
+    "uot_tensor3_workspace_size": (_SZ, [_I64, _I64, _I64]),
+    "uot_sinkhorn_tensor3": (ctypes.c_int, [_P, _I64, _I64, _I64, _P, _P, _P, _F, _F, _I32, _P,
+                                            _SZ, ctypes.POINTER(UotOptions), _P,
+                                            ctypes.POINTER(UotResult)]),
     "uot_batch_default_tuning": (None, [ctypes.POINTER(UotBatchTuning)]),
     "uot_batched_workspace_size": (_SZ, [ctypes.POINTER(UotProblem), _I32,
                                          ctypes.POINTER(UotOptions)]),
@@ -477,6 +481,35 @@ def uot_shard_finish(plan, beta, stream=None):
     _check(load().uot_shard_finish(pp, ldp, n, m, dtype_code(plan.dtype),
                                    _vector(beta, "beta", m), _stream(stream)),
            "uot_shard_finish")
+
+
+def uot_sinkhorn_tensor3(P, a, b, c, reg: float, reg_m: float, iters: int, ws=None,
+                         opt: UotOptions | None = None, stream=None, sync: bool = True,
+                         check_status: bool = True):
+    """Three-way form on the contiguous n1 x n2 x n3 tensor P, in place."""
+    torch = _torch()
+    if not P.is_cuda or P.dim() != 3 or not P.is_contiguous():
+        raise ValueError("P must be a contiguous 3-D CUDA tensor")
+    n1, n2, n3 = P.shape
+    opt = opt or options(dtype_code(P.dtype))
+    if ws is None:
+        size = int(load().uot_tensor3_workspace_size(n1, n2, n3))
+        if size == 0:
+            raise ValueError("bad tensor size")
+        ws = workspace_bytes(size, P.device)
+    res = UotResult()
+    st = load().uot_sinkhorn_tensor3(P.data_ptr(), n1, n2, n3, _vector(a, "a", n1),
+                                     _vector(b, "b", n2), _vector(c, "c", n3), float(reg),
+                                     float(reg_m), int(iters), ws.data_ptr(), ws.numel(),
+                                     ctypes.byref(opt), _stream(stream),
+                                     ctypes.byref(res) if sync else None)
+    if not sync:
+        _check(st, "uot_sinkhorn_tensor3")
+        return None
+    if st not in (UOT_OK, UOT_ERR_NONFINITE, UOT_ERR_ZERO_SUM, UOT_ERR_TIMEOUT) or (
+            check_status and st != UOT_OK):
+        raise UotError(st, "uot_sinkhorn_tensor3")
+    return SinkhornResult(res.iters_done, res.dev_status, res.err)
 
 
 def batch_tuning(stages: int | None = None, max_team: int | None = None,

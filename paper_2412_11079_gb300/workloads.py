@@ -20,6 +20,10 @@ Workloads (the plan is N x M; ``a`` has length N, ``b`` length M):
   [0.1, 10], marginals as in ``uniform2d``.
 * ``grad_batch`` -- problems of 16-D Gaussian points, C/max(C), marginals as in
   ``uniform2d``, reg 0.05, reg_m 1.0 (the differentiation case).
+* ``tensor3`` -- three-way problems: points x_i, y_j, z_k uniform in [0,1]^2,
+  C_ijk = |x_i - y_j|^2 + |y_j - z_k|^2 + |x_i - z_k|^2 (the sum of pairwise
+  squared distances), mode targets uniform(0.5, 1.5) normalised to masses
+  1.0, 1.5 and 1.2.
 """
 
 from __future__ import annotations
@@ -158,3 +162,46 @@ def grad_batch(seed: int = 0, count: int = 32, n: int = 2048, m: int = 2048,
         p.name = f"grad{k}_{n}x{m}"
         out.append(p)
     return out
+
+
+@dataclass
+class Problem3:
+    C: np.ndarray  # float32, (n1, n2, n3)
+    a: np.ndarray
+    b: np.ndarray
+    c: np.ndarray
+    reg: float
+    reg_m: float
+    iters: int
+
+    def __post_init__(self):
+        self.reg = float(np.float32(self.reg))
+        self.reg_m = float(np.float32(self.reg_m))
+
+
+def tensor3(seed: int = 0, n1: int = 64, n2: int = 48, n3: int = 40, reg: float = 0.1,
+            reg_m: float = 1.0, iters: int = 20) -> Problem3:
+    rng = np.random.default_rng(seed)
+    x, y, z = rng.random((n1, 2)), rng.random((n2, 2)), rng.random((n3, 2))
+    C = (sqdist(x, y)[:, :, None] + sqdist(y, z)[None, :, :] +
+         sqdist(x, z)[:, None, :]).astype(np.float32)
+    return Problem3(C, uniform_marginal(rng, n1, 1.0), uniform_marginal(rng, n2, 1.5),
+                    uniform_marginal(rng, n3, 1.2), reg, reg_m, iters)
+
+
+def tensor3_device(seed: int, n1: int, n2: int, n3: int, device, reg: float = 0.1,
+                   reg_m: float = 1.0):
+    """``tensor3`` with the cost tensor formed on the GPU (torch, FP64 then
+    FP32) for sizes where the host round trip dominates; same seeded points
+    and targets."""
+    import torch
+    rng = np.random.default_rng(seed)
+    x, y, z = rng.random((n1, 2)), rng.random((n2, 2)), rng.random((n3, 2))
+    a = uniform_marginal(rng, n1, 1.0)
+    b = uniform_marginal(rng, n2, 1.5)
+    c = uniform_marginal(rng, n3, 1.2)
+    tx, ty, tz = (torch.from_numpy(v).to(device) for v in (x, y, z))
+    C = (torch.cdist(tx, ty).square_()[:, :, None] + torch.cdist(ty, tz).square_()[None] +
+         torch.cdist(tx, tz).square_()[:, None, :]).to(torch.float32)
+    return (C, *(torch.from_numpy(v).to(device) for v in (a, b, c)),
+            float(np.float32(reg)), float(np.float32(reg_m)))
