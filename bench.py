@@ -685,7 +685,11 @@ def config_of(args, reference: bool = False):
         c.update({"plan_dtype": "f64", "algo": "FP64 numpy oracle (row step, then column step)",
                   "sample": "one iteration per step on the full plan"})
     else:
-        c.update({"plan_dtype": "f32", "algo": "fused one-pass, plan in place",
+        kform = getattr(args, "storage", "inplace") == "kform"
+        c.update({"plan_dtype": "f32",
+                  "algo": "fused one-pass, plan kept as K with FP32 scalings (kernel-form "
+                          "storage), written once at the end" if kform else
+                          "fused one-pass, plan in place",
                   "l2": "plan (1 GiB) larger than L2, no flush needed"})
     return c
 
@@ -703,7 +707,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "precision", "batched", "grad"])
+                    choices=["large", "precision", "batched", "grad", "small", "tensor"])
+    ap.add_argument("--storage", default="inplace", choices=["inplace", "kform"],
+                    help="large workload: how uot_sinkhorn keeps the plan (kform: the buffer "
+                         "kept as K with FP32 scalings)")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--nprob", type=int, default=512,
                     help="batched workload: number of problems")
@@ -745,6 +752,21 @@ def main():
             args.iters = 200
         run_batched(args)
         return
+    if args.workload == "small":
+        from paper_2412_11079_gb300 import build, uot
+        build.build()
+        uot.load()
+        n = 1024 if args.n == 16384 else args.n
+        print(json.dumps(measure_small(args, n, 100 if args.iters == 500 else args.iters,
+                                       args.steps)), flush=True)
+        return
+    if args.workload == "tensor":
+        from paper_2412_11079_gb300 import build, uot
+        build.build()
+        uot.load()
+        print(json.dumps(measure_tensor(args, 2048, 256, 100 if args.iters == 500 else args.iters,
+                                        args.steps)), flush=True)
+        return
     if args.workload == "precision":
         if args.n == 16384 and args.m == 16384:
             args.n = args.m = 32768
@@ -777,7 +799,8 @@ def main():
     b = torch.from_numpy(p.b).to(dev)
     plan = torch.empty((n, m), dtype=torch.float32, device=dev)
     cost = torch.empty(1, dtype=torch.float64, device=dev)
-    opt = uot.options()
+    storage = uot.UOT_STORAGE_KFORM if args.storage == "kform" else uot.UOT_STORAGE_INPLACE
+    opt = uot.options(storage=storage)
     ws = uot.workspace(n, m, opt, dev)
 
     def step(o):
@@ -800,7 +823,7 @@ def main():
     for e0, e1 in evs:
         e0.record(stream)  # torch creates the underlying cudaEvent on first record
         e1.record(stream)
-        o = uot.options()
+        o = uot.options(storage=storage)
         o.pass_events[0] = e0.cuda_event
         o.pass_events[1] = e1.cuda_event
         opts.append(o)
@@ -833,16 +856,17 @@ def main():
     assert res.dev_status == 0 and res.iters_done == iters
 
     # Roofline of the dominant kernel (the fused pass): algorithmic bytes per
-    # launch = one read and one write of the FP32 plan = 8*N*M.
+    # launch = one read and one write of the FP32 plan = 8*N*M (kernel-form
+    # storage: one read, 4*N*M).
     per_launch_s = pass_ms * 1e-3 / (args.steps * iters)
-    alg_bytes = 8.0 * n * m
+    alg_bytes = (4.0 if args.storage == "kform" else 8.0) * n * m
     achieved = alg_bytes / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as fh:
             tr = json.load(fh)
-        if tr.get("source_hash") == kernel_hash():
+        if tr.get("source_hash") == kernel_hash() and args.storage == "inplace":
             traffic = tr["bytes_per_elem"] * n * m
 
     # End to end through the public API from pinned host buffers: every step
@@ -1033,7 +1057,9 @@ def main():
             / (elapsed_ms * 1e-3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_kind": peak_kind, "kernel": "fused_pass_kernel<float,512,8>",
+                         "peak_kind": peak_kind,
+                         "kernel": "fused_pass_kernel<float,512,8>" +
+                                   (",KF (kernel-form storage)" if args.storage == "kform" else ""),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs: a device copy probe "
                                         "(read + write bytes over time), not a hard ceiling",
                          "frac_of_8TBs": achieved / 8000.0,
