@@ -410,7 +410,7 @@ def measure_grad(args, batch: int, n: int, iters: int, steps: int, warmup: int,
         U, V = torch.empty(n, device=dev), torch.empty(m, device=dev)
         hist = uot.workspace_bytes(int(uot.load().uot_grad_hist_size(n, m, iters)), dev)
         ws = uot.workspace(n, m, None, dev)
-        bws = uot.workspace_bytes(int(uot.load().uot_backward_workspace_size(n, m)), dev)
+        bws = uot.workspace_bytes(int(uot.load().uot_backward_workspace_size(n, m, iters)), dev)
         dC = torch.empty((n, ld), device=dev)[:, :m]
         da, db = torch.empty(n, device=dev), torch.empty(m, device=dev)
         cost = torch.empty(1, dtype=torch.float64, device=dev)
@@ -467,8 +467,14 @@ def measure_grad(args, batch: int, n: int, iters: int, steps: int, warmup: int,
         "unit": UNIT, "value": elems / (ms * 1e-3), "ms_per_step": ms,
         "forward_ms": fwd_ms, "backward_ms": ms - fwd_ms,
         "forward_value": elems / (fwd_ms * 1e-3),
-        "roofline": roofline_of("kform_pair_kernel<float> + reverse_pass_kernel (whole step)",
-                                elems * (4.0 + 12.0), ms * 1e-3, peak, peak_kind),
+        # Algorithmic bytes: K read once per forward iteration and once per
+        # reverse step (4 + 4 B per element and iteration), plus per problem
+        # the init (read C, write K), the adjoint's start (read K and C, write
+        # and re-read dl) and the final contraction's epilogue (read K and C,
+        # write dC): 8 + 16 + 12 B per element.
+        "roofline": roofline_of("kform_pair_kernel<float> + reverse_pass_kernel + bw_gemm_kernel "
+                                "(whole step)", elems * (4.0 + 4.0) + 36.0 * len(probs) * n * m,
+                                ms * 1e-3, peak, peak_kind),
         "branches": len(branches), "max_ctas_per_launch": args.grad_max_ctas,
         "max_ctas_per_adjoint_launch": args.grad_bwd_max_ctas,
     }
@@ -722,7 +728,7 @@ def main():
                     help="default run: skip the precision, batched and gradient comparisons")
     ap.add_argument("--grad-streams", type=int, default=16)
     ap.add_argument("--grad-max-ctas", type=int, default=80)
-    ap.add_argument("--grad-bwd-max-ctas", type=int, default=40)
+    ap.add_argument("--grad-bwd-max-ctas", type=int, default=80)
     ap.add_argument("--acc-n", type=int, default=8192)
     ap.add_argument("--shard", default="", choices=["", "rows"],
                     help="rows: the large problem's rows split over the ranks, column sums "

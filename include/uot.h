@@ -324,21 +324,23 @@ uot_status uot_sinkhorn_kform_save(const void* K, int64_t ldk, const float* a, c
  * respect to C (dC, n x m FP32, leading dimension lddc), a (da, n) and b
  * (db, m), for the solve recorded in `hist` by uot_sinkhorn_kform_save with
  * FP32 K = exp(-C/reg) (k_log2_scale 0) and the same iters, reg, reg_m.
- * Reverse steps t = T..1, one sweep each: Q_t = diag(U_t) K diag(V_{t-1})
- * and R_t = diag(U_{t-1}) K diag(V_{t-1}) are recomputed per row, the row
- * adjoint F and column adjoint G follow
+ * Reverse steps t = T..1, one read-only sweep of K each: Q_t =
+ * diag(U_t) K diag(V_{t-1}) and R_t = diag(U_{t-1}) K diag(V_{t-1}) are
+ * recomputed per row, the row adjoint F and column adjoint G follow
  *   w = -fi G / c_t,  db += fi G / b,  F += Q_t w,  G = (1 - fi) G,
  *   z = -fi F / r_t,  da += fi F / a,  G += R_t^T z, F = (1 - fi) F,
- * with dl += Q_t * w + R_t * z accumulated in the dC buffer, starting from
- * dl = P_T * C; finally dC = g (P_T - dl / reg), da and db times g, where
- * g = grad_out, times *grad_out_dev when grad_out_dev (one device double,
- * 8-byte aligned, read by the last launch) is not NULL -- so a caller whose
- * incoming gradient lives on the device need not synchronise.  K and dC must be
- * 16-byte aligned with ldk and lddc multiples of 4; m <= 8192.  The
- * workspace (uot_backward_workspace_size bytes, 256-byte aligned) is
+ * and dl = P_T * C + sum_t (Q_t * w + R_t * z) is formed once at the end
+ * from vectors each step records (the sum is K times a rank-2T matrix; one
+ * FP32 contraction of depth 2T), giving dC = g (P_T - dl / reg) and da, db
+ * times g, where g = grad_out, times *grad_out_dev when grad_out_dev (one
+ * device double, 8-byte aligned, read by the last launches) is not NULL --
+ * so a caller whose incoming gradient lives on the device need not
+ * synchronise.  K and dC must be 16-byte aligned with ldk and lddc multiples
+ * of 4; m <= 8192.  The workspace (uot_backward_workspace_size(n, m, iters)
+ * bytes, about (iters + 3) * 4 (2n + m) bytes, 256-byte aligned) is
  * caller-owned.  opt may be NULL; only opt->max_ctas is used.  Asynchronous.
  */
-size_t uot_backward_workspace_size(int64_t n, int64_t m);
+size_t uot_backward_workspace_size(int64_t n, int64_t m, int32_t iters);
 uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, int64_t ldc,
                                  const float* a, const float* b, int64_t n, int64_t m, float reg,
                                  float reg_m, int32_t iters, const void* hist, size_t hist_bytes,

@@ -11,12 +11,22 @@
 //                dl += Q_t * w, G = (1 - fi) G;
 //   row step:    z = -fi F / r_t, da += fi F / a, G += R_t^T z,
 //                dl += R_t * z, F = (1 - fi) F;
-// and dC = P_T - dl / reg.  Each reverse step is one sweep over the rows
-// with the same structure as the forward pass: Q_t and R_t are recomputed
-// per row from K and the saved scalings (never stored), the row reduction
-// (Q_t w)_i gives z_i, and R_t^T z is accumulated per column; dl is read and
-// written once per step (it lives in the dC buffer).  The last CTAs of a
-// step fold the column partials into G and prepare w for the next step.
+// and dC = P_T - dl / reg.  Each reverse step is one read-only sweep over
+// the rows of K with the same structure as the forward pass: Q_t and R_t are
+// recomputed per row from K and the saved scalings (never stored), the row
+// reduction (Q_t w)_i gives z_i, and R_t^T z is accumulated per column.  The
+// last CTAs of a step fold the column partials into G and prepare w for the
+// next step.
+//
+// dl is never updated in place.  Every step adds K (x) (q_t v_t w_t^T +
+// pz_t v_t^T) with per-step vectors q_t = U_t 2^-e_t, pz_t = U_{t-1} z_t
+// (rows) and v_t = V_{t-1}, v_t w_t (columns), so after all steps
+//     dl = P_T * C + K * (A B^T),  A = [q_1..q_T, pz_1..pz_T] (n x 2T),
+//                                  B = [v_1 w_1..v_T w_T, v_1..v_T] (m x 2T):
+// the steps record the 2T vectors (4 bytes per element of K per step instead
+// of reading and writing dl as well, 12), and one tiled FP32 contraction of
+// depth 2T with the final scaling fused (bw_gemm_kernel) writes dC at the
+// end.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,8 +45,6 @@ constexpr int BW_BETA_CTAS = 16;
 struct BwArgs {
   const float* K;
   int64_t ldk;
-  float* D;  // dl, in the dC buffer
-  int64_t ldd;
   int n, m, mpad;
   const float* a;
   const float* b;
@@ -63,6 +71,9 @@ struct BwArgs {
   int* slice_clear;
   Control* ctl;
   int stages;
+  float* Aq;       // (n): q_t = U_t 2^-e_t of this step's rows
+  float* Az;       // (n): pz_t = U_{t-1} z_t
+  float* Bw;       // (m): v_t w_t of this step's columns
 };
 
 template <int THREADS, int KV>
@@ -73,8 +84,8 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
   constexpr int ROW_BYTES = W * 4;
   extern __shared__ __align__(128) unsigned char smem[];
   const int stages = p.stages;
-  unsigned char* ring = smem;  // per slot: K row, then dl row
-  float* red = reinterpret_cast<float*>(smem + size_t(stages) * 2 * ROW_BYTES);
+  unsigned char* ring = smem;  // per slot: one row of K
+  float* red = reinterpret_cast<float*>(smem + size_t(stages) * ROW_BYTES);
   uint64_t* bars = reinterpret_cast<uint64_t*>(red + 2 * NW);
   int* slot_row = reinterpret_cast<int*>(bars + stages);
 
@@ -97,10 +108,9 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
     if (row >= 0 && row < n) {
       slot_row[slot] = row;
       if (copy_bytes) {
-        mbar_arrive_expect_tx(&bars[slot], 2 * copy_bytes);
-        unsigned char* dst = ring + size_t(slot) * 2 * ROW_BYTES;
-        bulk_load(dst, p.K + int64_t(row) * p.ldk, copy_bytes, &bars[slot], policy);
-        bulk_load(dst + ROW_BYTES, p.D + int64_t(row) * p.ldd, copy_bytes, &bars[slot], policy);
+        mbar_arrive_expect_tx(&bars[slot], copy_bytes);
+        bulk_load(ring + size_t(slot) * ROW_BYTES, p.K + int64_t(row) * p.ldk, copy_bytes,
+                  &bars[slot], policy);
       } else {
         mbar_arrive(&bars[slot]);
       }
@@ -126,6 +136,17 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
       v[k][e] = cc + e < m ? __ldcg(p.v + cc + e) : 0.0f;
       w[k][e] = cc + e < m ? __ldcg(p.w + cc + e) : 0.0f;
       h[k][e] = 0.0f;
+    }
+  }
+  // This step's column vector v_t w_t of the final contraction (every CTA
+  // covers all columns; one stores it).
+  if (blockIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      const int cc = (k * THREADS + tid) * VE;
+#pragma unroll
+      for (int e = 0; e < VE; ++e)
+        if (cc + e < m) p.Bw[cc + e] = v[k][e] * w[k][e];
     }
   }
   {
@@ -171,11 +192,9 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
     const float ri = cur[2];
     const float ai = cur[3];
     const float Fi = cur[4];
-    const unsigned char* sK = ring + size_t(slot) * 2 * ROW_BYTES;
-    const unsigned char* sD = sK + ROW_BYTES;
+    const unsigned char* sK = ring + size_t(slot) * ROW_BYTES;
     const float* gK = p.K + int64_t(row) * p.ldk;
-    float* gD = p.D + int64_t(row) * p.ldd;
-    float x[KV][VE], d[KV][VE];
+    float x[KV][VE];
     float s = 0.0f;
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
@@ -183,13 +202,9 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
       const int cc = li * VE;
       if (cc + VE <= m) {
         Elem<float>::unpack(ld_shared_v4(sK + size_t(li) * 16), x[k]);
-        Elem<float>::unpack(ld_shared_v4(sD + size_t(li) * 16), d[k]);
       } else {
 #pragma unroll
-        for (int e = 0; e < VE; ++e) {
-          x[k][e] = cc + e < m ? gK[cc + e] : 0.0f;
-          d[k][e] = cc + e < m ? gD[cc + e] : 0.0f;
-        }
+        for (int e = 0; e < VE; ++e) x[k][e] = cc + e < m ? gK[cc + e] : 0.0f;
       }
 #pragma unroll
       for (int e = 0; e < VE; ++e) s = fmaf(x[k][e] * v[k][e], w[k][e], s);
@@ -221,29 +236,17 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
     // Column step: F += (Q_t w)_i; row step: z, da, F.
     const float Fn = Fi + qi * S1;
     const float z = -p.fi * Fn / ri;
+    const float pz = pi * z;
     if (tid == 0) {
       p.da[row] += p.fi * Fn / ai;
       p.F[row] = (1.0f - p.fi) * Fn;
+      p.Aq[row] = qi;  // this step's row vectors of the final contraction
+      p.Az[row] = pz;
     }
-    const float pz = pi * z;
 #pragma unroll
-    for (int k = 0; k < KV; ++k) {
-      const int cc = (k * THREADS + tid) * VE;
-      float y[VE];
+    for (int k = 0; k < KV; ++k)
 #pragma unroll
-      for (int e = 0; e < VE; ++e) {
-        const float kv = x[k][e] * v[k][e];
-        h[k][e] = fmaf(kv, pz, h[k][e]);
-        y[e] = fmaf(kv, fmaf(qi, w[k][e], pz), d[k][e]);
-      }
-      if (cc + VE <= m) {
-        st_global_cs_v4(gD + cc, Elem<float>::pack(y));
-      } else {
-#pragma unroll
-        for (int e = 0; e < VE; ++e)
-          if (cc + e < m) gD[cc + e] = y[e];
-      }
-    }
+      for (int e = 0; e < VE; ++e) h[k][e] = fmaf(x[k][e] * v[k][e], pz, h[k][e]);
     ++done_rows;
   }
   if (done_rows > 0) {
@@ -329,24 +332,110 @@ __global__ void bw_cols_kernel(const float* G0, const float* cT, const float* b,
   Gs[j] = (1.0f - fi) * G;
 }
 
-// dC = g (P_T - dl / reg), da *= g, db *= g, with g = grad_out times the
-// optional device scalar (read here, so the caller need not synchronise).
-__global__ void __launch_bounds__(TB) bw_final_kernel(const float* K, int64_t ldk, const float* U,
-                                                      const float* V, float* D, int64_t ldd,
-                                                      int n, int m, float inv_reg, double g_host,
-                                                      const double* g_dev, float* da, float* db) {
-  const float g = float(g_dev ? g_host * *g_dev : g_host);
-  const int j = blockIdx.x * TB + threadIdx.x;
-  if (blockIdx.y == 0) {
-    for (int i = j; i < n; i += gridDim.x * TB) da[i] *= g;
-    if (j < m) db[j] *= g;
+// The final contraction: acc = A B^T over the 2T recorded step vectors
+// (A_s = q_t or pz_t of the rows, B_s = v_t w_t or v_t of the columns), then
+//     dl = P_T * C + K * acc,   dC = g (P_T - dl / reg),
+// with g = grad_out times the optional device scalar (read here, so the
+// caller need not synchronise).  FP32 on the CUDA cores (the depth-2T sum
+// needs FP32 accuracy): 128 x 128 tiles, 16 steps of depth per stage in
+// shared memory, 8 x 8 outputs per thread.
+constexpr int GB = 128, GKD = 16, GT = 256;
+
+struct BwGemmArgs {
+  const float* K;
+  int64_t ldk;
+  const float* C;
+  int64_t ldc;
+  float* D;
+  int64_t ldd;
+  const float* UT;  // U_T (n)
+  const float* VT;  // V_T (m)
+  const float* Aq;  // q_t at Aq + (t-1) sn
+  const float* Az;  // pz_t at Az + (t-1) sn
+  const float* Bw;  // v_t w_t at Bw + (t-1) sm
+  const float* Vh;  // V_{t-1} at Vh + (t-1) sv (the history)
+  int64_t sn, sm, sv;
+  int n, m, T;
+  float inv_reg;
+  double g_host;
+  const double* g_dev;
+};
+
+__global__ void __launch_bounds__(GT) bw_gemm_kernel(const BwGemmArgs p) {
+  __shared__ __align__(16) float As[GKD][GB];
+  __shared__ __align__(16) float Bs[GKD][GB];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int i0 = blockIdx.y * GB, j0 = blockIdx.x * GB;
+  const int S = 2 * p.T;
+  float acc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.0f;
+  const int lk = threadIdx.x / 16, l8 = (threadIdx.x % 16) * 8;  // loader: depth row, 8 entries
+  for (int s0 = 0; s0 < S; s0 += GKD) {
+    {
+      const int sidx = s0 + lk;
+      const float* arow = nullptr;
+      const float* brow = nullptr;
+      if (sidx < p.T) {
+        arow = p.Aq + sidx * p.sn;
+        brow = p.Bw + sidx * p.sm;
+      } else if (sidx < S) {
+        arow = p.Az + (sidx - p.T) * p.sn;
+        brow = p.Vh + (sidx - p.T) * p.sv;
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int i = i0 + l8 + e, j = j0 + l8 + e;
+        As[lk][l8 + e] = (arow && i < p.n) ? __ldg(arow + i) : 0.0f;
+        Bs[lk][l8 + e] = (brow && j < p.m) ? __ldg(brow + j) : 0.0f;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GKD; ++kk) {
+      float a[8], b[8];
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
+      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+      a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+      b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
   }
-  if (j >= m) return;
-  const float v = V[j];
-  for (int i = blockIdx.y; i < n; i += gridDim.y) {
-    const float P = (U[i] * K[int64_t(i) * ldk + j]) * v;
-    float* dp = D + int64_t(i) * ldd + j;
-    *dp = g * (P - *dp * inv_reg);
+  const float g = float(p.g_dev ? p.g_host * *p.g_dev : p.g_host);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = i0 + ty * 8 + r;
+    if (i >= p.n) continue;
+    const float u = p.UT[i];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = j0 + tx * 8 + c;
+      if (j >= p.m) continue;
+      const float k = p.K[int64_t(i) * p.ldk + j];
+      const float P = (u * k) * p.VT[j];
+      const float dl = fmaf(k, acc[r][c], P * p.C[int64_t(i) * p.ldc + j]);
+      p.D[int64_t(i) * p.ldd + j] = g * (P - dl * p.inv_reg);
+    }
+  }
+}
+
+// da *= g, db *= g.
+__global__ void bw_scale_kernel(float* da, int n, float* db, int m, double g_host,
+                                const double* g_dev) {
+  const float g = float(g_dev ? g_host * *g_dev : g_host);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(n, m); i += gridDim.x * blockDim.x) {
+    if (i < n) da[i] *= g;
+    if (i < m) db[i] *= g;
   }
 }
 
@@ -380,15 +469,21 @@ constexpr int kBwNum = int(sizeof(kBw) / sizeof(kBw[0]));
 
 size_t bw_smem(const BwEntry& e, int stages) {
   const size_t row = size_t(e.threads) * e.kv * 16;
-  return size_t(stages) * 2 * row + 2 * (e.threads / 32) * 4 + size_t(stages) * 12;
+  return size_t(stages) * row + 2 * (e.threads / 32) * 4 + size_t(stages) * 12;
 }
 
+// Backward workspace: the adjoint state (cleared at the start of a call),
+// then the step vectors of the final contraction (T rows each, written
+// before they are read).
 struct BwLayout {
-  size_t ctl, F, da, w, Gs, G0, h[3], ctr, total;
+  size_t ctl, F, da, w, Gs, G0, h[3], ctr, state_end, Aq, Az, Bw, total;
+  size_t npad, mpad;  // floats
 };
-BwLayout bw_layout(int64_t n, int64_t m) {
+BwLayout bw_layout(int64_t n, int64_t m, int T) {
   BwLayout L{};
-  const size_t npad = size_t((n + 63) & ~int64_t(63)) * 4, mpad = size_t((m + 63) & ~int64_t(63)) * 4;
+  L.npad = size_t((n + 63) & ~int64_t(63));
+  L.mpad = size_t((m + 63) & ~int64_t(63));
+  const size_t npad = L.npad * 4, mpad = L.mpad * 4;
   size_t off = 0;
   L.ctl = off; off = align256(off + sizeof(Control));
   L.F = off; off = align256(off + npad);
@@ -398,6 +493,10 @@ BwLayout bw_layout(int64_t n, int64_t m) {
   L.G0 = off; off = align256(off + mpad);
   for (int k = 0; k < 3; ++k) { L.h[k] = off; off = align256(off + mpad); }
   L.ctr = off; off = align256(off + 9 * sizeof(int));
+  L.state_end = off;
+  L.Aq = off; off = align256(off + size_t(T) * npad);
+  L.Az = off; off = align256(off + size_t(T) * npad);
+  L.Bw = off; off = align256(off + size_t(T) * mpad);
   L.total = off;
   return L;
 }
@@ -427,9 +526,9 @@ size_t uot_grad_hist_size(int64_t n, int64_t m, int32_t iters) {
   return hist_layout(n, m, iters).total;
 }
 
-size_t uot_backward_workspace_size(int64_t n, int64_t m) {
-  if (n < 1 || m < 1 || n > INT32_MAX || m > INT32_MAX / 2) return 0;
-  return bw_layout(n, m).total;
+size_t uot_backward_workspace_size(int64_t n, int64_t m, int32_t iters) {
+  if (n < 1 || m < 1 || iters < 0 || n > INT32_MAX || m > INT32_MAX / 2) return 0;
+  return bw_layout(n, m, iters).total;
 }
 
 uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, int64_t ldc,
@@ -454,7 +553,7 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
   const int T = iters, N = int(n), M = int(m);
   const HistLayout HL = hist_layout(n, m, T);
   if (hist_bytes < HL.total) return UOT_ERR_INVALID_ARG;
-  const BwLayout L = bw_layout(n, m);
+  const BwLayout L = bw_layout(n, m, T);
   if (!workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(workspace) % 256)
     return UOT_ERR_WORKSPACE;
   int k = -1;
@@ -478,7 +577,10 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
   int* ctr = reinterpret_cast<int*>(ws + L.ctr);
   Control* ctl = reinterpret_cast<Control*>(ws + L.ctl);
 
-  if (cudaMemsetAsync(ws, 0, L.total, s) != cudaSuccess) return UOT_ERR_CUDA;
+  if (cudaMemsetAsync(ws, 0, L.state_end, s) != cudaSuccess) return UOT_ERR_CUDA;
+  float* Aq = reinterpret_cast<float*>(ws + L.Aq);
+  float* Az = reinterpret_cast<float*>(ws + L.Az);
+  float* Bw = reinterpret_cast<float*>(ws + L.Bw);
   {
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
@@ -542,8 +644,6 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
   BwArgs A{};
   A.K = K;
   A.ldk = ldk;
-  A.D = dC;
-  A.ldd = lddc;
   A.n = N;
   A.m = M;
   A.mpad = int((m + 63) & ~int64_t(63));
@@ -574,19 +674,44 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
     A.arrive_clear = ctr + 3 + (q + 1) % 3;
     A.slice_ctr = ctr + 6 + q % 3;
     A.slice_clear = ctr + 6 + (q + 1) % 3;
+    A.Aq = Aq + size_t(t - 1) * L.npad;
+    A.Az = Az + size_t(t - 1) * L.npad;
+    A.Bw = Bw + size_t(t - 1) * L.mpad;
     void* kargs[] = {&A};
     if (cudaLaunchKernel(e.fn, dim3(grid), dim3(e.threads), kargs, smem, s) != cudaSuccess)
       return UOT_ERR_CUDA;
     count_launch();
   }
   {
-    const int gx = (M + TB - 1) / TB;
-    int gy = (sms * 8 + gx - 1) / gx;
-    gy = std::max(1, std::min(gy, std::min(N, 65535)));
-    bw_final_kernel<<<dim3(gx, gy), TB, 0, s>>>(K, ldk, U_t(T), V_t(T), dC, lddc, N, M, 1.0f / reg,
-                                              grad_out, grad_out_dev, da, db);
+    BwGemmArgs G{};
+    G.K = K;
+    G.ldk = ldk;
+    G.C = C;
+    G.ldc = ldc;
+    G.D = dC;
+    G.ldd = lddc;
+    G.UT = U_t(T);
+    G.VT = V_t(T);
+    G.Aq = Aq;
+    G.Az = Az;
+    G.Bw = Bw;
+    G.Vh = V_t(0);
+    G.sn = int64_t(L.npad);
+    G.sm = int64_t(L.mpad);
+    G.sv = int64_t(HL.strideV / 4);
+    G.n = N;
+    G.m = M;
+    G.T = T;
+    G.inv_reg = 1.0f / reg;
+    G.g_host = grad_out;
+    G.g_dev = grad_out_dev;
+    const dim3 gg((M + GB - 1) / GB, (N + GB - 1) / GB);
+    bw_gemm_kernel<<<gg, GT, 0, s>>>(G);
     if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
-    count_launch();
+    bw_scale_kernel<<<std::max(1, std::min((std::max(N, M) + 255) / 256, sms * 4)), 256, 0, s>>>(
+        da, N, db, M, grad_out, grad_out_dev);
+    if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
+    count_launch(2);
   }
   return UOT_OK;
 }

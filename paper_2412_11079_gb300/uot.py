@@ -98,7 +98,7 @@ SIGNATURES = {
                                                _P, _P, _P, _SZ, _P, _SZ,
                                                ctypes.POINTER(UotOptions), _P,
                                                ctypes.POINTER(UotResult)]),
-    "uot_backward_workspace_size": (_SZ, [_I64, _I64]),
+    "uot_backward_workspace_size": (_SZ, [_I64, _I64, _I32]),
     "uot_sinkhorn_backward": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _P, _I64, _I64, _F, _F,
                                              _I32, _P, _SZ, _D, _P, _P, _I64, _P, _P, _P, _SZ,
                                              ctypes.POINTER(UotOptions), _P]),
@@ -611,7 +611,7 @@ def uot_sinkhorn_backward(K, C, a, b, reg: float, reg_m: float, iters: int, hist
     da = torch.empty(n, device=K.device) if da is None else da
     db = torch.empty(m, device=K.device) if db is None else db
     if ws is None:
-        ws = workspace_bytes(int(load().uot_backward_workspace_size(n, m)), K.device)
+        ws = workspace_bytes(int(load().uot_backward_workspace_size(n, m, int(iters))), K.device)
     kp, ldk = _matrix(K, "K")
     cp, ldc = _matrix(C, "C")
     gp, ldd = _matrix(dC, "dC")
