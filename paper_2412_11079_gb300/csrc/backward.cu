@@ -102,7 +102,14 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
   }
   __syncthreads();
   const uint64_t policy = policy_evict_first();
-  int issued = 0, next_row = n;
+  // Static schedule: CTA g owns the contiguous rows [g R, (g+1) R), so the
+  // ring is armed without a shared counter and the rows' scalars are loaded
+  // in coalesced chunks ahead of use (a row here is only m floats of K; the
+  // per-row round trips of a dynamic schedule would bound the step).
+  const int R = (n + int(gridDim.x) - 1) / int(gridDim.x);
+  const int r0 = int(blockIdx.x) * R;
+  const int nrows = max(0, min(n, r0 + R) - r0);
+  int issued = 0;
   auto arm = [&](int q, int row) {
     const int slot = q % stages;
     if (row >= 0 && row < n) {
@@ -120,10 +127,8 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
     }
   };
   if (tid == 0) {
-    const int base = atomicAdd(p.row_ctr, stages);
-    for (int q = 0; q < stages; ++q) arm(q, base + q);
+    for (int q = 0; q < stages; ++q) arm(q, q < nrows ? r0 + q : -1);
     issued = stages;
-    if (base + stages < n) next_row = atomicAdd(p.row_ctr, 1);
   }
 
   // This step's column values: V'_{t-1} and w.
@@ -161,18 +166,23 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
 
   bool broken = false;
   int done_rows = 0;
-  // Per-row values of the next step, loaded one step ahead (its row was
-  // armed before this step's barrier) so their latency overlaps this step.
-  float pf[5];
-  bool have_pf = false;
-  auto fetch_row = [&](int row, float (&v5)[5]) {
-    v5[0] = __ldcg(p.q + row);
-    v5[1] = __ldcg(p.pr + row);
-    v5[2] = __ldcg(p.r + row);
-    v5[3] = __ldg(p.a + row);
-    v5[4] = __ldcg(p.F + row);
-  };
+  // Per-row values (q, pr, r, a, F) of the CTA's rows, a chunk of RCH rows at
+  // a time.
+  constexpr int RCH = 64;
+  __shared__ float sc[5][RCH];
   for (int q = 0;; ++q) {
+    if (q % RCH == 0 && q < nrows) {  // uniform for the CTA
+      __syncthreads();  // every thread is done with the previous chunk
+      for (int i = tid; i < min(RCH, nrows - q); i += THREADS) {
+        const int row = r0 + q + i;
+        sc[0][i] = __ldcg(p.q + row);
+        sc[1][i] = __ldcg(p.pr + row);
+        sc[2][i] = __ldcg(p.r + row);
+        sc[3][i] = __ldg(p.a + row);
+        sc[4][i] = __ldcg(p.F + row);
+      }
+      __syncthreads();
+    }
     const int slot = q % stages;
     if (!broken && !mbar_wait_bounded(&bars[slot], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS)) {
       broken = true;
@@ -180,18 +190,12 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
     }
     const int row = *reinterpret_cast<volatile int*>(&slot_row[slot]);
     if (row < 0 || row >= n) break;
-    float cur[5];
-    if (have_pf) {
-#pragma unroll
-      for (int i = 0; i < 5; ++i) cur[i] = pf[i];
-    } else {
-      fetch_row(row, cur);
-    }
-    const float qi = cur[0] * qscale;
-    const float pi = cur[1];
-    const float ri = cur[2];
-    const float ai = cur[3];
-    const float Fi = cur[4];
+    const int ci = q % RCH;
+    const float qi = sc[0][ci] * qscale;
+    const float pi = sc[1][ci];
+    const float ri = sc[2][ci];
+    const float ai = sc[3][ci];
+    const float Fi = sc[4][ci];
     const unsigned char* sK = ring + size_t(slot) * ROW_BYTES;
     const float* gK = p.K + int64_t(row) * p.ldk;
     float x[KV][VE];
@@ -217,18 +221,9 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
       st |= DEV_TIMEOUT;
       break;
     }
-    {
-      // Step q + 1 was armed at step q + 1 - stages (or before the loop),
-      // ahead of this barrier; its slot is re-armed only after the next one.
-      const int nrow = *reinterpret_cast<volatile int*>(&slot_row[(q + 1) % stages]);
-      have_pf = nrow >= 0 && nrow < n;
-      if (have_pf) fetch_row(nrow, pf);
-    }
     if (tid == 0 && !broken) {
-      const int r2 = next_row;
-      arm(issued, r2);
+      arm(issued, issued < nrows ? r0 + issued : -1);
       ++issued;
-      if (r2 < n) next_row = atomicAdd(p.row_ctr, 1);
     }
     float S1 = 0.0f;
 #pragma unroll
