@@ -400,45 +400,56 @@ def measure_grad(args, batch: int, n: int, iters: int, steps: int, warmup: int,
     peak, peak_kind = measured_peaks()
     m = n
     probs = workloads.grad_batch(seed=0, count=batch, n=n, m=m, iters=iters)
+    B = len(probs)
     ld = (m + 3) // 4 * 4
-    bufs = []
-    for p in probs:
-        C = torch.from_numpy(p.C).to(dev)
-        a = torch.from_numpy(p.a).to(dev)
-        b = torch.from_numpy(p.b).to(dev)
-        K = torch.empty((n, ld), device=dev)[:, :m]
-        U, V = torch.empty(n, device=dev), torch.empty(m, device=dev)
-        hist = uot.workspace_bytes(int(uot.load().uot_grad_hist_size(n, m, iters)), dev)
-        ws = uot.workspace(n, m, None, dev)
-        bws = uot.workspace_bytes(int(uot.load().uot_backward_workspace_size(n, m, iters)), dev)
-        dC = torch.empty((n, ld), device=dev)[:, :m]
-        da, db = torch.empty(n, device=dev), torch.empty(m, device=dev)
-        cost = torch.empty(1, dtype=torch.float64, device=dev)
-        bufs.append((p, C, a, b, K, U, V, hist, ws, bws, dC, da, db, cost))
+    # A uniform batch: [B, n, m] tensors, so the adjoint of the whole batch is
+    # one set of launches (one reverse launch per step for all problems).
+    C3 = torch.stack([torch.from_numpy(p.C) for p in probs]).to(dev)
+    a2 = torch.stack([torch.from_numpy(p.a) for p in probs]).to(dev)
+    b2 = torch.stack([torch.from_numpy(p.b) for p in probs]).to(dev)
+    K3 = torch.empty((B, n, ld), device=dev)[:, :, :m]
+    U2, V2 = torch.empty((B, n), device=dev), torch.empty((B, m), device=dev)
+    hist2 = uot.grad_hist_batch(B, n, m, iters, dev)
+    wss = [uot.workspace(n, m, None, dev) for _ in range(B)]
+    dC3 = torch.empty((B, n, ld), device=dev)[:, :, :m]
+    da2, db2 = torch.empty((B, n), device=dev), torch.empty((B, m), device=dev)
+    cost = torch.empty(B, dtype=torch.float64, device=dev)
+    per_problem = args.grad_backward == "per-problem"
+    if per_problem:
+        bwss = [uot.workspace_bytes(int(uot.load().uot_backward_workspace_size(n, m, iters)), dev)
+                for _ in range(B)]
+    else:
+        bws = uot.workspace_bytes(
+            int(uot.load().uot_backward_batch_workspace_size(B, n, m, iters)), dev)
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
-    # The problems run as parallel branches (one stream each), every launch
-    # limited to a share of the GPU, so the fixed cost of each 16 MB pass
-    # overlaps with the other problems' passes.
-    branches = [torch.cuda.Stream() for _ in range(min(args.grad_streams, len(bufs)))]
+    # The forward solves run as parallel branches (one stream each), every
+    # launch limited to a share of the GPU, so the fixed cost of each 16 MB
+    # pass overlaps with the other problems' passes.
+    branches = [torch.cuda.Stream() for _ in range(min(args.grad_streams, B))]
     opt = uot.options(max_ctas=args.grad_max_ctas)
-    # The adjoint's launches are limited separately: a reverse step (12 bytes
-    # per element, one row per step) overlapped best in narrower launches.
     bopt = uot.options(max_ctas=args.grad_bwd_max_ctas)
+    reg, reg_m = probs[0].reg, probs[0].reg_m
 
     def step(s, backward=True):
         for br in branches:
             br.wait_stream(s)
-        for i, (p, C, a, b, K, U, V, hist, ws, bws, dC, da, db, cost) in enumerate(bufs):
+        for i in range(B):
             bs = branches[i % len(branches)]
-            uot.uot_init_kernel(C, K, p.reg, stream=bs)
-            uot.uot_sinkhorn_kform_save(K, a, b, p.reg, p.reg_m, iters, U, V, hist, ws, bs, opt)
+            uot.uot_init_kernel(C3[i], K3[i], reg, stream=bs)
+            uot.uot_sinkhorn_kform_save(K3[i], a2[i], b2[i], reg, reg_m, iters, U2[i], V2[i],
+                                        hist2[i], wss[i], bs, opt)
             if backward:
-                uot.uot_kform_cost(K, U, V, C, cost, bs)
-                uot.uot_sinkhorn_backward(K, C, a, b, p.reg, p.reg_m, iters, hist, 1.0, dC, da,
-                                          db, bws, bs, bopt)
+                uot.uot_kform_cost(K3[i], U2[i], V2[i], C3[i], cost[i:i + 1], bs)
+                if per_problem:
+                    uot.uot_sinkhorn_backward(K3[i], C3[i], a2[i], b2[i], reg, reg_m, iters,
+                                              hist2[i], 1.0, dC3[i], da2[i], db2[i], bwss[i],
+                                              bs, bopt)
         for br in branches:
             s.wait_stream(br)
+        if backward and not per_problem:
+            uot.uot_sinkhorn_backward_batch(K3, C3, a2, b2, reg, reg_m, iters, hist2, 1.0, dC3,
+                                            da2, db2, bws, s)
 
     def timed_graph(backward):
         g = torch.cuda.CUDAGraph()
@@ -475,10 +486,12 @@ def measure_grad(args, batch: int, n: int, iters: int, steps: int, warmup: int,
         "roofline": roofline_of("kform_pair_kernel<float> + reverse_pass_kernel + bw_gemm_kernel "
                                 "(whole step)", elems * (4.0 + 4.0) + 36.0 * len(probs) * n * m,
                                 ms * 1e-3, peak, peak_kind),
-        "branches": len(branches), "max_ctas_per_launch": args.grad_max_ctas,
-        "max_ctas_per_adjoint_launch": args.grad_bwd_max_ctas,
+        "forward_branches": len(branches), "max_ctas_per_forward_launch": args.grad_max_ctas,
+        "adjoint": ("per problem, on the forward's branches, launches of <= "
+                    f"{args.grad_bwd_max_ctas} CTAs" if per_problem else
+                    "batched: one reverse launch per step for all problems"),
     }
-    del bufs
+    del C3, K3, dC3, wss, hist2
     torch.cuda.empty_cache()
     if check_iters:
         # Gradient errors of the first problem at the full size against the
@@ -728,7 +741,9 @@ def main():
                     help="default run: skip the precision, batched and gradient comparisons")
     ap.add_argument("--grad-streams", type=int, default=16)
     ap.add_argument("--grad-max-ctas", type=int, default=80)
-    ap.add_argument("--grad-bwd-max-ctas", type=int, default=80)
+    ap.add_argument("--grad-bwd-max-ctas", type=int, default=80,
+                    help="CTA cap of the per-problem adjoint's launches")
+    ap.add_argument("--grad-backward", choices=["batched", "per-problem"], default="batched")
     ap.add_argument("--acc-n", type=int, default=8192)
     ap.add_argument("--shard", default="", choices=["", "rows"],
                     help="rows: the large problem's rows split over the ranks, column sums "

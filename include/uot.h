@@ -348,6 +348,33 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
                                  int64_t lddc, float* da, float* db, void* workspace,
                                  size_t ws_bytes, const uot_options* opt, void* stream);
 
+/*
+ * uot_sinkhorn_backward_batch -- uot_sinkhorn_backward for `batch` problems
+ * of one shape (n x m, iters, reg, reg_m) in one set of launches: each
+ * reverse step is a single launch over a grid of problems x row blocks,
+ * instead of one launch per problem and step.  Problem k's K, C and dC
+ * start stride_k, stride_c and stride_dc elements after problem 0's (same
+ * leading dimensions; stride_k and stride_dc multiples of 4; no overlap),
+ * its history hist_stride bytes after problem 0's (>= uot_grad_hist_size,
+ * a multiple of 256; hist 256-byte aligned), and a, b, da, db are packed
+ * [batch][n] / [batch][m].  grad_out multiplies every problem's gradients;
+ * grad_out_dev, when not NULL, holds `batch` device doubles (problem k's
+ * factor).  The workspace is uot_backward_batch_workspace_size(batch, n, m,
+ * iters) bytes, 256-byte aligned, caller-owned.  opt->max_ctas caps the
+ * CTAs of a reverse launch over the whole batch.  1 <= batch <= 65535.
+ * Otherwise as uot_sinkhorn_backward (which is this call with batch 1).
+ */
+size_t uot_backward_batch_workspace_size(int32_t batch, int64_t n, int64_t m, int32_t iters);
+uot_status uot_sinkhorn_backward_batch(int32_t batch, const float* K, int64_t ldk,
+                                       int64_t stride_k, const float* C, int64_t ldc,
+                                       int64_t stride_c, const float* a, const float* b,
+                                       int64_t n, int64_t m, float reg, float reg_m,
+                                       int32_t iters, const void* hist, size_t hist_stride,
+                                       double grad_out, const double* grad_out_dev, float* dC,
+                                       int64_t lddc, int64_t stride_dc, float* da, float* db,
+                                       void* workspace, size_t ws_bytes, const uot_options* opt,
+                                       void* stream);
+
 /* Synchronises `stream` and reads the result of the last uot_sinkhorn call
  * that used `workspace` (same n, m, opt).  Returns the device status as a
  * uot_status as uot_sinkhorn does with a non-NULL `out`. */

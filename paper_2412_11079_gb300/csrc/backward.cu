@@ -15,8 +15,9 @@
 // the rows of K with the same structure as the forward pass: Q_t and R_t are
 // recomputed per row from K and the saved scalings (never stored), the row
 // reduction (Q_t w)_i gives z_i, and R_t^T z is accumulated per column.  The
-// last CTAs of a step fold the column partials into G and prepare w for the
-// next step.
+// next step's CTAs fold those column partials into G as they start (each
+// forms w for its own columns; every column's db and G are written by one of
+// them).
 //
 // dl is never updated in place.  Every step adds K (x) (q_t v_t w_t^T +
 // pz_t v_t^T) with per-step vectors q_t = U_t 2^-e_t, pz_t = U_{t-1} z_t
@@ -40,35 +41,43 @@ namespace uot {
 
 namespace {
 
-constexpr int BW_BETA_CTAS = 16;
+// A uniform batch: problem k's data sits at fixed strides from problem 0's.
+struct BwBatch {
+  int64_t sK, sC, sD;  // elements between problems' K, C and dC
+  size_t sH, sW;       // bytes between problems' histories and workspaces
+};
 
+template <typename P>
+__device__ __forceinline__ P* at_bytes(P* x, size_t off) {  // x advanced by off bytes
+  return reinterpret_cast<P*>(reinterpret_cast<uintptr_t>(x) + off);
+}
+
+// One reverse step of every problem of the batch; problem 0's pointers.
 struct BwArgs {
+  BwBatch B;
   const float* K;
   int64_t ldk;
   int n, m, mpad;
-  const float* a;
-  const float* b;
+  int cpp;         // CTAs per problem (the grid is batch x cpp)
+  const float* a;  // [batch][n]
+  const float* b;  // [batch][m]
   float fi;
   int t;           // reverse step (iteration index)
+  int first;       // t = T: db is assigned rather than accumulated
   const double* log2k;  // gauge of the forward solve: Q_t = K U'_t V'_{t-1} 2^-e_t
   const float* q;  // U'_t (n)
   const float* pr; // U'_{t-1} (n)
   const float* v;  // V'_{t-1} (mpad)
   const float* r;  // r_t (n)
-  const float* c_prev;  // c_{t-1} (mpad), for the next step's w (t > 1)
+  const float* c;  // c_t (mpad), for this step's w
   float* F;        // row adjoints (n)
-  float* da;       // (n)
-  float* w;        // (mpad): w of this step, overwritten with the next step's
-  float* Gs;       // (mpad): (1 - fi) G entering this step's row part
-  float* db;       // (mpad)
+  float* da;       // [batch][n]
+  const float* Gs_in;   // (mpad): (1 - fi) G after the previous step's column step
+  const float* h_prev;  // (mpad): R^T z of the previous step (colsum(dl) at t = T)
+  float* Gs_out;   // (mpad): (1 - fi) G after this step's column step
+  float* db;       // [batch][m]
   float* h_next;   // (mpad) column partials R_t^T z, pre-zeroed
   float* h_clear;  // buffer to clear for the next step
-  int* row_ctr;
-  int* ctr_clear;
-  int* arrive;
-  int* arrive_clear;
-  int* slice_ctr;
-  int* slice_clear;
   Control* ctl;
   int stages;
   float* Aq;       // (n): q_t = U_t 2^-e_t of this step's rows
@@ -76,22 +85,53 @@ struct BwArgs {
   float* Bw;       // (m): v_t w_t of this step's columns
 };
 
-template <int THREADS, int KV>
-__global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p) {
+// CTA (k, g) of the grid takes problem k's contiguous rows [g R, (g+1) R).
+// Each thread holds VE * KV columns: vw = v w for the row reductions
+// (Q_t w)_i = U_t,i sum_j K_ij v_j w_j and the column partials
+// hh_j = sum_i K_ij pz_i (h = v hh once the block is done).  The row loop is
+// software-pipelined: after the barrier that publishes row q's reduction,
+// every thread loads row q+1 from the ring and reduces it while it finishes
+// row q (pz_q and its column partials), so one barrier per row carries both
+// and the two dependency chains overlap.  A row's scalars come from a
+// shared chunk loaded 64 rows at a time, and its outputs (F, da, the step
+// vectors) are written back per chunk, coalesced: nothing on a row's path
+// waits on global memory.
+template <int THREADS, int KV, bool TAIL>
+__global__ void __launch_bounds__(THREADS, (512 / THREADS > 1 ? 512 / THREADS : 1))
+    reverse_pass_kernel(const BwArgs p) {
   constexpr int VE = 4;
   constexpr int NW = THREADS / 32;
   constexpr int W = KV * VE * THREADS;
   constexpr int ROW_BYTES = W * 4;
+  constexpr int RCH = 64;
   extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ float sc[6][RCH];  // q 2^-e, U_{t-1}, r, a, F, da of the chunk's rows
+  __shared__ float so[2][RCH];  // F + (Q_t w)_i and pz of the chunk's rows
   const int stages = p.stages;
   unsigned char* ring = smem;  // per slot: one row of K
-  float* red = reinterpret_cast<float*>(smem + size_t(stages) * ROW_BYTES);
+  float* red = reinterpret_cast<float*>(smem + size_t(stages) * ROW_BYTES);  // [2][NW]
   uint64_t* bars = reinterpret_cast<uint64_t*>(red + 2 * NW);
-  int* slot_row = reinterpret_cast<int*>(bars + stages);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = p.n, m = p.m;
-  const float qscale = ldexpf(1.0f, -gauge_exponent(p.t, float(*p.log2k)));
+  const int prob = int(blockIdx.x) / p.cpp, lb = int(blockIdx.x) - prob * p.cpp;
+  const size_t oh = size_t(prob) * p.B.sH, ow = size_t(prob) * p.B.sW;
+  const float* K = p.K + int64_t(prob) * p.B.sK;
+  const float* av = p.a + int64_t(prob) * n;
+  const float* bv = p.b + int64_t(prob) * m;
+  float* da = p.da + int64_t(prob) * n;
+  float* db = p.db + int64_t(prob) * m;
+  const float* qv = at_bytes(p.q, oh);
+  const float* prv = at_bytes(p.pr, oh);
+  const float* vv = at_bytes(p.v, oh);
+  const float* rv = at_bytes(p.r, oh);
+  float* F = at_bytes(p.F, ow);
+  float* h_next = at_bytes(p.h_next, ow);
+  float* Aq = at_bytes(p.Aq, ow);
+  float* Az = at_bytes(p.Az, ow);
+  Control* ctl = at_bytes(p.ctl, ow);
+  const float qscale =
+      ldexpf(1.0f, -gauge_exponent(p.t, float(*at_bytes(p.log2k, oh))));
   const uint32_t copy_bytes = uint32_t((size_t(m) * 4) & ~size_t(15));
   uint32_t st = 0;
 
@@ -102,192 +142,237 @@ __global__ void __launch_bounds__(THREADS, 1) reverse_pass_kernel(const BwArgs p
   }
   __syncthreads();
   const uint64_t policy = policy_evict_first();
-  // Static schedule: CTA g owns the contiguous rows [g R, (g+1) R), so the
-  // ring is armed without a shared counter and the rows' scalars are loaded
-  // in coalesced chunks ahead of use (a row here is only m floats of K; the
-  // per-row round trips of a dynamic schedule would bound the step).
-  const int R = (n + int(gridDim.x) - 1) / int(gridDim.x);
-  const int r0 = int(blockIdx.x) * R;
+  const int R = (n + p.cpp - 1) / p.cpp;
+  const int r0 = lb * R;
   const int nrows = max(0, min(n, r0 + R) - r0);
-  int issued = 0;
-  auto arm = [&](int q, int row) {
+  int armed = 0;  // rows armed so far (thread 0)
+  auto arm = [&](int q) {  // row q of the block into slot q % stages
+    if (q >= nrows) return;
     const int slot = q % stages;
-    if (row >= 0 && row < n) {
-      slot_row[slot] = row;
-      if (copy_bytes) {
-        mbar_arrive_expect_tx(&bars[slot], copy_bytes);
-        bulk_load(ring + size_t(slot) * ROW_BYTES, p.K + int64_t(row) * p.ldk, copy_bytes,
-                  &bars[slot], policy);
-      } else {
-        mbar_arrive(&bars[slot]);
-      }
+    if (copy_bytes) {
+      mbar_arrive_expect_tx(&bars[slot], copy_bytes);
+      bulk_load(ring + size_t(slot) * ROW_BYTES, K + int64_t(r0 + q) * p.ldk, copy_bytes,
+                &bars[slot], policy);
     } else {
-      slot_row[slot] = -1;
       mbar_arrive(&bars[slot]);
     }
+    armed = q + 1;
   };
-  if (tid == 0) {
-    for (int q = 0; q < stages; ++q) arm(q, q < nrows ? r0 + q : -1);
-    issued = stages;
-  }
+  if (tid == 0)
+    for (int q = 0; q < stages; ++q) arm(q);
 
-  // This step's column values: V'_{t-1} and w.
-  float v[KV][VE], w[KV][VE], h[KV][VE];
+  // Column step: G = (1 - fi) G + R^T z of the previous step, w = -fi G / c_t,
+  // db += fi G / b; the CTA that owns column j (j / ceil(m / cpp) == its
+  // index) writes db_j and (1 - fi) G_j for the next step.
+  float vw[KV][VE], hh[KV][VE];
+  {
+    const float* gin = at_bytes(p.Gs_in, ow);
+    const float* hprev = at_bytes(p.h_prev, ow);
+    const float* ct = at_bytes(p.c, oh);
+    float* gout = at_bytes(p.Gs_out, ow);
+    const int own = (m + p.cpp - 1) / p.cpp;
 #pragma unroll
-  for (int k = 0; k < KV; ++k) {
-    const int cc = (k * THREADS + tid) * VE;
+    for (int k = 0; k < KV; ++k) {
+      const int cc = (k * THREADS + tid) * VE;
 #pragma unroll
-    for (int e = 0; e < VE; ++e) {
-      v[k][e] = cc + e < m ? __ldcg(p.v + cc + e) : 0.0f;
-      w[k][e] = cc + e < m ? __ldcg(p.w + cc + e) : 0.0f;
-      h[k][e] = 0.0f;
+      for (int e = 0; e < VE; ++e) {
+        const int j = cc + e;
+        hh[k][e] = 0.0f;
+        vw[k][e] = 0.0f;
+        if (j < m) {
+          const float G = __ldcg(gin + j) + __ldcg(hprev + j);
+          vw[k][e] = __ldcg(vv + j) * (-p.fi * G / __ldcg(ct + j));
+          if (j / own == lb) {
+            db[j] = (p.first ? 0.0f : db[j]) + p.fi * G / __ldg(bv + j);
+            gout[j] = (1.0f - p.fi) * G;
+          }
+        }
+      }
     }
   }
-  // This step's column vector v_t w_t of the final contraction (every CTA
-  // covers all columns; one stores it).
-  if (blockIdx.x == 0) {
+  // This step's column vector v_t w_t of the final contraction (every CTA of
+  // the problem holds all columns; its first one stores them).
+  if (lb == 0) {
+    float* Bw = at_bytes(p.Bw, ow);
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
       const int cc = (k * THREADS + tid) * VE;
 #pragma unroll
       for (int e = 0; e < VE; ++e)
-        if (cc + e < m) p.Bw[cc + e] = v[k][e] * w[k][e];
+        if (cc + e < m) Bw[cc + e] = vw[k][e];
     }
   }
   {
-    const int g = blockIdx.x * THREADS + tid, gs = gridDim.x * THREADS;
-    for (int j = g; j < p.mpad; j += gs) p.h_clear[j] = 0.0f;
-    if (blockIdx.x == 0 && tid == 0) {
-      *p.ctr_clear = 0;
-      *p.arrive_clear = 0;
-      *p.slice_clear = 0;
-    }
+    float* h_clear = at_bytes(p.h_clear, ow);
+    for (int j = lb * THREADS + tid; j < p.mpad; j += p.cpp * THREADS) h_clear[j] = 0.0f;
   }
 
-  bool broken = false;
-  int done_rows = 0;
-  // Per-row values (q, pr, r, a, F) of the CTA's rows, a chunk of RCH rows at
-  // a time.
-  constexpr int RCH = 64;
-  __shared__ float sc[5][RCH];
-  for (int q = 0;; ++q) {
-    if (q % RCH == 0 && q < nrows) {  // uniform for the CTA
-      __syncthreads();  // every thread is done with the previous chunk
-      for (int i = tid; i < min(RCH, nrows - q); i += THREADS) {
-        const int row = r0 + q + i;
-        sc[0][i] = __ldcg(p.q + row);
-        sc[1][i] = __ldcg(p.pr + row);
-        sc[2][i] = __ldcg(p.r + row);
-        sc[3][i] = __ldg(p.a + row);
-        sc[4][i] = __ldcg(p.F + row);
-      }
-      __syncthreads();
+  auto load_chunk = [&](int q0) {
+    for (int i = tid; i < min(RCH, nrows - q0); i += THREADS) {
+      const int row = r0 + q0 + i;
+      const float qi = __ldcg(qv + row) * qscale;
+      sc[0][i] = qi;
+      sc[1][i] = __ldcg(prv + row);
+      sc[2][i] = __ldcg(rv + row);
+      sc[3][i] = __ldg(av + row);
+      sc[4][i] = __ldcg(F + row);
+      sc[5][i] = __ldcg(da + row);
+      Aq[row] = qi;  // this step's row vectors of the final contraction
     }
+  };
+  // Column step: F += (Q_t w)_i; row step: z, da += fi F / a, F = (1 - fi) F.
+  auto flush = [&](int q0, int cnt) {
+    for (int i = tid; i < cnt; i += THREADS) {
+      const int row = r0 + q0 + i;
+      const float Fn = so[0][i];
+      da[row] = sc[5][i] + p.fi * Fn / sc[3][i];
+      F[row] = (1.0f - p.fi) * Fn;
+      Az[row] = so[1][i];
+    }
+  };
+  bool broken = false;
+  auto load_row = [&](int q, float (&x)[KV][VE]) {
     const int slot = q % stages;
     if (!broken && !mbar_wait_bounded(&bars[slot], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS)) {
       broken = true;
       st |= DEV_TIMEOUT;
     }
-    const int row = *reinterpret_cast<volatile int*>(&slot_row[slot]);
-    if (row < 0 || row >= n) break;
-    const int ci = q % RCH;
-    const float qi = sc[0][ci] * qscale;
-    const float pi = sc[1][ci];
-    const float ri = sc[2][ci];
-    const float ai = sc[3][ci];
-    const float Fi = sc[4][ci];
     const unsigned char* sK = ring + size_t(slot) * ROW_BYTES;
-    const float* gK = p.K + int64_t(row) * p.ldk;
-    float x[KV][VE];
-    float s = 0.0f;
+    const float* gK = K + int64_t(r0 + q) * p.ldk;
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
       const int li = k * THREADS + tid;
       const int cc = li * VE;
-      if (cc + VE <= m) {
+      if (!TAIL || cc + VE <= m) {  // without TAIL every vector is in the slot
         Elem<float>::unpack(ld_shared_v4(sK + size_t(li) * 16), x[k]);
       } else {
 #pragma unroll
         for (int e = 0; e < VE; ++e) x[k][e] = cc + e < m ? gK[cc + e] : 0.0f;
       }
+    }
+  };
+  auto dot = [&](const float (&x)[KV][VE]) {
+    float s4[VE];
 #pragma unroll
-      for (int e = 0; e < VE; ++e) s = fmaf(x[k][e] * v[k][e], w[k][e], s);
-    }
-    s = warp_sum(s);
-    float* rb = red + (q & 1) * NW;
-    if (lane == 0) rb[warp] = s;
-    if (__syncthreads_or(broken ? 1 : 0)) {
-      broken = true;
-      st |= DEV_TIMEOUT;
-      break;
-    }
-    if (tid == 0 && !broken) {
-      arm(issued, issued < nrows ? r0 + issued : -1);
-      ++issued;
-    }
+    for (int e = 0; e < VE; ++e) s4[e] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KV; ++k)
+#pragma unroll
+      for (int e = 0; e < VE; ++e) s4[e] = fmaf(x[k][e], vw[k][e], s4[e]);
+    return warp_sum((s4[0] + s4[1]) + (s4[2] + s4[3]));
+  };
+  auto finish_row = [&](int q, const float (&x)[KV][VE]) {
+    const float* rb = red + (q & 1) * NW;
     float S1 = 0.0f;
 #pragma unroll
     for (int k = 0; k < NW; ++k) S1 += rb[k];
-    // Column step: F += (Q_t w)_i; row step: z, da, F.
-    const float Fn = Fi + qi * S1;
-    const float z = -p.fi * Fn / ri;
-    const float pz = pi * z;
+    const int ci = q % RCH;
+    const float Fn = sc[4][ci] + sc[0][ci] * S1;
+    const float pz = sc[1][ci] * (-p.fi * Fn / sc[2][ci]);
     if (tid == 0) {
-      p.da[row] += p.fi * Fn / ai;
-      p.F[row] = (1.0f - p.fi) * Fn;
-      p.Aq[row] = qi;  // this step's row vectors of the final contraction
-      p.Az[row] = pz;
+      so[0][ci] = Fn;
+      so[1][ci] = pz;
     }
 #pragma unroll
     for (int k = 0; k < KV; ++k)
 #pragma unroll
-      for (int e = 0; e < VE; ++e) h[k][e] = fmaf(x[k][e] * v[k][e], pz, h[k][e]);
-    ++done_rows;
-  }
-  if (done_rows > 0) {
+      for (int e = 0; e < VE; ++e) hh[k][e] = fmaf(x[k][e], pz, hh[k][e]);
+  };
+
+  if (nrows > 0) {
+    load_chunk(0);
+    float xc[KV][VE];
+    load_row(0, xc);
+    {
+      const float s0 = dot(xc);
+      if (lane == 0) red[warp] = s0;
+    }
+    bool stop = __syncthreads_or(broken ? 1 : 0) != 0;
+    if (!stop) {
+      if (tid == 0) arm(stages);  // row 0 is in every thread's registers
+      // Row q is in xc, row q + 1 goes to xn; the next step swaps the roles
+      // (the loop is unrolled by two, so no registers are copied).
+      auto step = [&](int q, const float (&xc)[KV][VE], float (&xn)[KV][VE]) {
+        if (q > 0 && q % RCH == 0) {  // uniform; rows < q are finished
+          flush(q - RCH, RCH);
+          __syncthreads();
+          load_chunk(q);
+          __syncthreads();
+        }
+        const bool nx = q + 1 < nrows;
+        float sn = 0.0f;
+        if (nx) {
+          load_row(q + 1, xn);
+          sn = dot(xn);
+        }
+        finish_row(q, xc);
+        if (nx && lane == 0) red[((q + 1) & 1) * NW + warp] = sn;
+        if (__syncthreads_or(broken ? 1 : 0)) return false;
+        if (nx && tid == 0) arm(q + 1 + stages);
+        return true;
+      };
+      float xd[KV][VE];
+      for (int q = 0; q < nrows; q += 2) {
+        if (!step(q, xc, xd)) {
+          stop = true;
+          break;
+        }
+        if (q + 1 < nrows && !step(q + 1, xd, xc)) {
+          stop = true;
+          break;
+        }
+      }
+    }
+    if (stop) {
+      broken = true;
+      st |= DEV_TIMEOUT;
+    } else {
+      const int q0 = ((nrows - 1) / RCH) * RCH;
+      flush(q0, nrows - q0);  // the last barrier published so[] of every row
+    }
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
       const int cc = (k * THREADS + tid) * VE;
       if (cc + VE <= m) {
-        red_add_v4(p.h_next + cc, h[k][0], h[k][1], h[k][2], h[k][3]);
+        red_add_v4(h_next + cc, __ldcg(vv + cc) * hh[k][0], __ldcg(vv + cc + 1) * hh[k][1],
+                   __ldcg(vv + cc + 2) * hh[k][2], __ldcg(vv + cc + 3) * hh[k][3]);
       } else {
 #pragma unroll
         for (int e = 0; e < VE; ++e)
-          if (cc + e < m) atomicAdd(p.h_next + cc + e, h[k][e]);
+          if (cc + e < m) atomicAdd(h_next + cc + e, __ldcg(vv + cc + e) * hh[k][e]);
       }
     }
   }
-  if (st) atomicOr(&p.ctl->status, st);
-  // The CTAs that finish last: G = (1 - fi) G_prev + R_t^T z; db and the next
-  // step's w (claimed in column slices once every CTA's partials landed).
-  {
-    const int nsl = 64;
-    const int per = (m + nsl - 1) / nsl;
-    finish_pass_job(p.arrive, p.slice_ctr, nsl, BW_BETA_CTAS, 2000, [&](int sl) {
-      const int j0 = sl * per, j1 = min(m, j0 + per);
-      for (int j = j0 + tid; j < j1; j += THREADS) {
-        const float Gj = p.Gs[j] + __ldcg(p.h_next + j);
-        if (p.t > 1) {
-          p.db[j] += p.fi * Gj / __ldg(p.b + j);
-          p.w[j] = -p.fi * Gj / __ldcg(p.c_prev + j);
-          p.Gs[j] = (1.0f - p.fi) * Gj;
-        }
-      }
-    });
-  }
-  if (tid == 0 && broken) {
-    for (int q = max(0, issued - stages); q < issued; ++q)
+  if (st) atomicOr(&ctl->status, st);
+  if (tid == 0 && broken) {  // let the copies in flight land before exiting
+    for (int q = max(0, armed - stages); q < armed; ++q)
       mbar_wait_bounded(&bars[q % stages], uint32_t(q / stages) & 1u, WAIT_LIMIT_NS);
   }
 }
 
 constexpr int TB = 256;
 
-// dl = P_T * C with P_T = (U_i K_ij) V_j; F = rowsum(dl) (one warp per row).
+// Clears the adjoint state of every problem's workspace (grid.y = problem).
+__global__ void __launch_bounds__(TB) bw_zero_kernel(unsigned char* ws, size_t bytes, size_t sW) {
+  uint4* z = reinterpret_cast<uint4*>(ws + size_t(blockIdx.y) * sW);
+  for (size_t i = blockIdx.x * size_t(TB) + threadIdx.x; i < bytes / 16; i += size_t(gridDim.x) * TB)
+    z[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// dl = P_T * C with P_T = (U_i K_ij) V_j; F = rowsum(dl) (one warp per row;
+// grid.y = problem).
 __global__ void __launch_bounds__(TB) bw_init_kernel(const float* K, int64_t ldk, const float* C,
                                                      int64_t ldc, const float* U, const float* V,
                                                      float* D, int64_t ldd, int n, int m,
-                                                     float* F, float* da) {
+                                                     float* F, float* da, BwBatch B) {
+  const int k = blockIdx.y;
+  K += int64_t(k) * B.sK;
+  C += int64_t(k) * B.sC;
+  D += int64_t(k) * B.sD;
+  U = at_bytes(U, size_t(k) * B.sH);
+  V = at_bytes(V, size_t(k) * B.sH);
+  F = at_bytes(F, size_t(k) * B.sW);
+  da += int64_t(k) * n;
   const int warp = (blockIdx.x * TB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int nw = (gridDim.x * TB) >> 5;
   for (int i = warp; i < n; i += nw) {
@@ -306,25 +391,17 @@ __global__ void __launch_bounds__(TB) bw_init_kernel(const float* K, int64_t ldk
   }
 }
 
-// G0 = colsum(dl): a column per thread over a stride of rows, then atomics.
+// G0 = colsum(dl): a column per thread over a stride of rows, then atomics
+// (grid.z = problem).
 __global__ void __launch_bounds__(TB) bw_colsum_kernel(const float* D, int64_t ldd, int n, int m,
-                                                       float* G0) {
+                                                       float* G0, BwBatch B) {
   const int j = blockIdx.x * TB + threadIdx.x;
   if (j >= m) return;
+  D += int64_t(blockIdx.z) * B.sD;
+  G0 = at_bytes(G0, size_t(blockIdx.z) * B.sW);
   float s = 0.0f;
   for (int i = blockIdx.y; i < n; i += gridDim.y) s += D[int64_t(i) * ldd + j];
   atomicAdd(G0 + j, s);
-}
-
-// w_T = -fi G0 / c_T, db = fi G0 / b, Gs = (1 - fi) G0.
-__global__ void bw_cols_kernel(const float* G0, const float* cT, const float* b, float fi, int m,
-                               float* w, float* db, float* Gs) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
-  const float G = G0[j];
-  w[j] = -fi * G / cT[j];
-  db[j] = fi * G / b[j];
-  Gs[j] = (1.0f - fi) * G;
 }
 
 // The final contraction: acc = A B^T over the 2T recorded step vectors
@@ -353,10 +430,25 @@ struct BwGemmArgs {
   int n, m, T;
   float inv_reg;
   double g_host;
-  const double* g_dev;
+  const double* g_dev;  // one per problem, or NULL
+  BwBatch B;
 };
 
-__global__ void __launch_bounds__(GT) bw_gemm_kernel(const BwGemmArgs p) {
+__global__ void __launch_bounds__(GT) bw_gemm_kernel(BwGemmArgs p) {
+  {  // problem blockIdx.z of the batch
+    const int k = blockIdx.z;
+    const size_t oh = size_t(k) * p.B.sH, ow = size_t(k) * p.B.sW;
+    p.K += int64_t(k) * p.B.sK;
+    p.C += int64_t(k) * p.B.sC;
+    p.D += int64_t(k) * p.B.sD;
+    p.UT = at_bytes(p.UT, oh);
+    p.VT = at_bytes(p.VT, oh);
+    p.Vh = at_bytes(p.Vh, oh);
+    p.Aq = at_bytes(p.Aq, ow);
+    p.Az = at_bytes(p.Az, ow);
+    p.Bw = at_bytes(p.Bw, ow);
+    if (p.g_dev) p.g_dev += k;
+  }
   __shared__ __align__(16) float As[GKD][GB];
   __shared__ __align__(16) float Bs[GKD][GB];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -424,10 +516,12 @@ __global__ void __launch_bounds__(GT) bw_gemm_kernel(const BwGemmArgs p) {
   }
 }
 
-// da *= g, db *= g.
+// da *= g, db *= g (grid.y = problem).
 __global__ void bw_scale_kernel(float* da, int n, float* db, int m, double g_host,
                                 const double* g_dev) {
-  const float g = float(g_dev ? g_host * *g_dev : g_host);
+  da += int64_t(blockIdx.y) * n;
+  db += int64_t(blockIdx.y) * m;
+  const float g = float(g_dev ? g_host * g_dev[blockIdx.y] : g_host);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(n, m); i += gridDim.x * blockDim.x) {
     if (i < n) da[i] *= g;
     if (i < m) db[i] *= g;
@@ -454,10 +548,13 @@ __global__ void bw_hist_init_kernel(uint8_t* hist, HistLayout L, int n, int m, i
 
 struct BwEntry {
   int threads, kv;
-  const void* fn;
+  const void* fn[2];  // [rows of a multiple of 4 columns, any width]
 };
-#define BW_ENTRY(TH, KV) \
-  BwEntry { TH, KV, reinterpret_cast<const void*>(&reverse_pass_kernel<TH, KV>) }
+#define BW_ENTRY(TH, KV)                                                        \
+  BwEntry {                                                                      \
+    TH, KV, {reinterpret_cast<const void*>(&reverse_pass_kernel<TH, KV, false>), \
+             reinterpret_cast<const void*>(&reverse_pass_kernel<TH, KV, true>)}  \
+  }
 // Four vectors per thread (four warps for rows of 2048 columns, four CTAs
 // per SM): a reverse step's CTA barrier per row is cheapest with few warps,
 // and the per-row latency is hidden by CTAs side by side rather than by wider
@@ -468,14 +565,14 @@ constexpr int kBwNum = int(sizeof(kBw) / sizeof(kBw[0]));
 
 size_t bw_smem(const BwEntry& e, int stages) {
   const size_t row = size_t(e.threads) * e.kv * 16;
-  return size_t(stages) * row + 2 * (e.threads / 32) * 4 + size_t(stages) * 12;
+  return size_t(stages) * row + 2 * (e.threads / 32) * 4 + size_t(stages) * 8;
 }
 
 // Backward workspace: the adjoint state (cleared at the start of a call),
 // then the step vectors of the final contraction (T rows each, written
 // before they are read).
 struct BwLayout {
-  size_t ctl, F, da, w, Gs, G0, h[3], ctr, state_end, Aq, Az, Bw, total;
+  size_t ctl, F, Gs[2], G0, h[3], state_end, Aq, Az, Bw, total;
   size_t npad, mpad;  // floats
 };
 BwLayout bw_layout(int64_t n, int64_t m, int T) {
@@ -486,12 +583,9 @@ BwLayout bw_layout(int64_t n, int64_t m, int T) {
   size_t off = 0;
   L.ctl = off; off = align256(off + sizeof(Control));
   L.F = off; off = align256(off + npad);
-  L.da = off; off = align256(off + npad);
-  L.w = off; off = align256(off + mpad);
-  L.Gs = off; off = align256(off + mpad);
+  for (int k = 0; k < 2; ++k) { L.Gs[k] = off; off = align256(off + mpad); }
   L.G0 = off; off = align256(off + mpad);
   for (int k = 0; k < 3; ++k) { L.h[k] = off; off = align256(off + mpad); }
-  L.ctr = off; off = align256(off + 9 * sizeof(int));
   L.state_end = off;
   L.Aq = off; off = align256(off + size_t(T) * npad);
   L.Az = off; off = align256(off + size_t(T) * npad);
@@ -501,7 +595,7 @@ BwLayout bw_layout(int64_t n, int64_t m, int T) {
 }
 
 std::mutex g_bw_mu;
-size_t g_bw_smem_set[64][kBwNum];
+size_t g_bw_smem_set[64][kBwNum][2];
 
 }  // namespace
 
@@ -530,14 +624,21 @@ size_t uot_backward_workspace_size(int64_t n, int64_t m, int32_t iters) {
   return bw_layout(n, m, iters).total;
 }
 
-uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, int64_t ldc,
-                                 const float* a, const float* b, int64_t n, int64_t m, float reg,
-                                 float reg_m, int32_t iters, const void* hist, size_t hist_bytes,
-                                 double grad_out, const double* grad_out_dev, float* dC,
-                                 int64_t lddc, float* da, float* db, void* workspace,
-                                 size_t ws_bytes, const uot_options* opt, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// The adjoint of `batch` problems of one shape; problem k's arrays at the
+// given strides from problem 0's (a, b, da, db packed: n or m apart).
+uot_status backward_run(int32_t batch, const float* K, int64_t ldk, int64_t sK, const float* C,
+                        int64_t ldc, int64_t sC, const float* a, const float* b, int64_t n,
+                        int64_t m, float reg, float reg_m, int32_t iters, const void* hist,
+                        size_t hist_bytes, size_t sH, double grad_out,
+                        const double* grad_out_dev, float* dC, int64_t lddc, int64_t sD,
+                        float* da, float* db, void* workspace, size_t ws_bytes,
+                        const uot_options* opt, void* stream) {
   const int max_ctas = opt ? opt->max_ctas : 0;
-  if (max_ctas < 0) return UOT_ERR_INVALID_ARG;
+  if (max_ctas < 0 || batch < 1 || batch > 65535) return UOT_ERR_INVALID_ARG;
   if (!K || !C || !a || !b || !hist || !dC || !da || !db || n < 1 || m < 1 || n > INT32_MAX ||
       m > INT32_MAX / 2 || ldk < m || ldc < m || lddc < m)
     return UOT_ERR_INVALID_ARG;
@@ -548,19 +649,29 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
       ldk % 4 || lddc % 4)
     return UOT_ERR_INVALID_ARG;  // rows of K and dC are fetched with bulk copies
   if (iters < 0) return UOT_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int T = iters, N = int(n), M = int(m);
   const HistLayout HL = hist_layout(n, m, T);
   if (hist_bytes < HL.total) return UOT_ERR_INVALID_ARG;
+  if (batch > 1) {  // problems neither overlap nor lose the alignment of problem 0
+    if (sK < (n - 1) * ldk + m || sC < (n - 1) * ldc + m || sD < (n - 1) * lddc + m ||
+        sK % 4 || sD % 4 || sH < HL.total || sH % 256 ||
+        reinterpret_cast<uintptr_t>(hist) % 256)
+      return UOT_ERR_INVALID_ARG;
+  }
   const BwLayout L = bw_layout(n, m, T);
-  if (!workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(workspace) % 256)
+  if (!workspace || ws_bytes / size_t(batch) < L.total ||
+      reinterpret_cast<uintptr_t>(workspace) % 256)
     return UOT_ERR_WORKSPACE;
   int k = -1;
   for (int i = 0; i < kBwNum; ++i)
-    if (kBw[i].threads * kBw[i].kv * 4 >= M && (k < 0 || kBw[i].threads * kBw[i].kv < kBw[k].threads * kBw[k].kv))
+    if (kBw[i].threads * kBw[i].kv * 4 >= M &&
+        (k < 0 || kBw[i].threads * kBw[i].kv < kBw[k].threads * kBw[k].kv))
       k = i;
   if (k < 0) return UOT_ERR_UNSUPPORTED;  // rows wider than one CTA (8192 columns)
+  if ((N + GB - 1) / GB > 65535) return UOT_ERR_UNSUPPORTED;
 
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const BwBatch Bt{sK, sC, sD, sH, L.total};
   const double fi_d = std::isinf(reg_m) ? 1.0 : double(reg_m) / (double(reg_m) + double(reg));
   const float fi = float(fi_d);
   uint8_t* ws = static_cast<uint8_t*>(workspace);
@@ -570,44 +681,39 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
   auto r_t = [&](int t) { return reinterpret_cast<const float*>(hb + HL.r + size_t(t) * HL.strideU); };
   auto c_t = [&](int t) { return reinterpret_cast<const float*>(hb + HL.c + size_t(t) * HL.strideV); };
   float* F = reinterpret_cast<float*>(ws + L.F);
-  float* w = reinterpret_cast<float*>(ws + L.w);
-  float* Gs = reinterpret_cast<float*>(ws + L.Gs);
   float* G0 = reinterpret_cast<float*>(ws + L.G0);
-  int* ctr = reinterpret_cast<int*>(ws + L.ctr);
   Control* ctl = reinterpret_cast<Control*>(ws + L.ctl);
-
-  if (cudaMemsetAsync(ws, 0, L.state_end, s) != cudaSuccess) return UOT_ERR_CUDA;
   float* Aq = reinterpret_cast<float*>(ws + L.Aq);
   float* Az = reinterpret_cast<float*>(ws + L.Az);
   float* Bw = reinterpret_cast<float*>(ws + L.Bw);
-  {
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    bw_init_kernel<<<sms * 8, TB, 0, s>>>(K, ldk, C, ldc, U_t(T), V_t(T), dC, lddc, N, M, F, da);
-    if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
-    count_launch();
-    const int gx = (M + TB - 1) / TB;
-    const int gy = std::max(1, std::min(std::min(N, 65535), (sms * 8 + gx - 1) / gx));
-    bw_colsum_kernel<<<dim3(gx, gy), TB, 0, s>>>(dC, lddc, N, M, G0);
-    if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
-    count_launch();
-  }
-  if (T > 0) {
-    bw_cols_kernel<<<(M + 255) / 256, 256, 0, s>>>(G0, c_t(T), b, fi, M, w, db, Gs);
-    if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
-    count_launch();
-  } else {
-    if (cudaMemsetAsync(db, 0, size_t(M) * 4, s) != cudaSuccess) return UOT_ERR_CUDA;
-  }
 
-  // Geometry of the reverse pass.
-  const BwEntry& e = kBw[k];
   int dev = 0, sms = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return UOT_ERR_CUDA;
+  const int per_prob = std::max(1, sms * 8 / batch);  // blocks of the one-off kernels
+  bw_zero_kernel<<<dim3(std::max(1, std::min(per_prob, int(L.state_end / (16 * TB)) + 1)), batch),
+                   TB, 0, s>>>(ws, L.state_end, L.total);
+  if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
+  bw_init_kernel<<<dim3(per_prob, batch), TB, 0, s>>>(K, ldk, C, ldc, U_t(T), V_t(T), dC, lddc,
+                                                      N, M, F, da, Bt);
+  if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
+  {
+    const int gx = (M + TB - 1) / TB;
+    const int gy = std::max(1, std::min(std::min(N, 65535), (per_prob + gx - 1) / gx));
+    bw_colsum_kernel<<<dim3(gx, gy, batch), TB, 0, s>>>(dC, lddc, N, M, G0, Bt);
+    if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
+  }
+  count_launch(3);
+  if (T == 0 && cudaMemsetAsync(db, 0, size_t(batch) * size_t(M) * 4, s) != cudaSuccess)
+    return UOT_ERR_CUDA;
+
+  // Geometry of the reverse pass: as many CTAs as fit on the GPU at once,
+  // shared evenly among the problems (at least two rows each).
+  const BwEntry& e = kBw[k];
+  const int tail = M % 4 ? 1 : 0;
+  const void* fn = e.fn[tail];
   int stages = 2, occ = 0;
   for (int st = 8; st >= 2; --st)
     if (bw_smem(e, st) <= size_t(optin)) {
@@ -620,14 +726,14 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
     const size_t b2 = bw_smem(e, st);
     {
       std::lock_guard<std::mutex> lock(g_bw_mu);
-      if (dev < 64 && g_bw_smem_set[dev][k] < b2) {
-        if (cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b2)) !=
+      if (dev < 64 && g_bw_smem_set[dev][k][tail] < b2) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b2)) !=
             cudaSuccess)
           return UOT_ERR_CUDA;
-        g_bw_smem_set[dev][k] = b2;
+        g_bw_smem_set[dev][k][tail] = b2;
       }
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e.fn, e.threads, b2) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, e.threads, b2) != cudaSuccess)
       return UOT_ERR_CUDA;
     if (occ == 0) break;
     if (st == 2) best_occ = occ;
@@ -636,48 +742,49 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
   }
   if (best_occ == 0) return UOT_ERR_CUDA;
   const size_t smem = bw_smem(e, best_st);
-  int grid = best_occ * sms;
-  if (grid > (N + 1) / 2) grid = std::max(1, (N + 1) / 2);
-  if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+  int total = best_occ * sms;
+  if (max_ctas > 0 && total > max_ctas) total = max_ctas;
+  const int cpp = std::max(1, std::min(total / batch, (N + 1) / 2));
 
   BwArgs A{};
+  A.B = Bt;
   A.K = K;
   A.ldk = ldk;
   A.n = N;
   A.m = M;
   A.mpad = int((m + 63) & ~int64_t(63));
+  A.cpp = cpp;
   A.a = a;
   A.b = b;
   A.fi = fi;
   A.F = F;
   A.da = da;
-  A.w = w;
-  A.Gs = Gs;
   A.db = db;
   A.ctl = ctl;
   A.stages = best_st;
+  A.log2k = reinterpret_cast<const double*>(hb);  // HistHeader::log2k
   for (int t = T; t >= 1; --t) {
     const int q = T - t;  // pass counter for the rings
     A.t = t;
-    A.log2k = reinterpret_cast<const double*>(hb);  // HistHeader::log2k
+    A.first = q == 0;
     A.q = U_t(t);
     A.pr = U_t(t - 1);
     A.v = V_t(t - 1);
     A.r = r_t(t);
-    A.c_prev = t > 1 ? c_t(t - 1) : c_t(t);
+    A.c = c_t(t);
+    // G enters step T as colsum(dl) (Gs zero); later steps fold the previous
+    // step's partials.  h cycles through three buffers: the previous step's
+    // (read), this step's (accumulated) and the next step's (cleared).
+    A.Gs_in = reinterpret_cast<const float*>(ws + L.Gs[q % 2]);
+    A.Gs_out = reinterpret_cast<float*>(ws + L.Gs[(q + 1) % 2]);
+    A.h_prev = q == 0 ? G0 : reinterpret_cast<const float*>(ws + L.h[(q + 2) % 3]);
     A.h_next = reinterpret_cast<float*>(ws + L.h[q % 3]);
     A.h_clear = reinterpret_cast<float*>(ws + L.h[(q + 1) % 3]);
-    A.row_ctr = ctr + q % 3;
-    A.ctr_clear = ctr + (q + 1) % 3;
-    A.arrive = ctr + 3 + q % 3;
-    A.arrive_clear = ctr + 3 + (q + 1) % 3;
-    A.slice_ctr = ctr + 6 + q % 3;
-    A.slice_clear = ctr + 6 + (q + 1) % 3;
     A.Aq = Aq + size_t(t - 1) * L.npad;
     A.Az = Az + size_t(t - 1) * L.npad;
     A.Bw = Bw + size_t(t - 1) * L.mpad;
     void* kargs[] = {&A};
-    if (cudaLaunchKernel(e.fn, dim3(grid), dim3(e.threads), kargs, smem, s) != cudaSuccess)
+    if (cudaLaunchKernel(fn, dim3(batch * cpp), dim3(e.threads), kargs, smem, s) != cudaSuccess)
       return UOT_ERR_CUDA;
     count_launch();
   }
@@ -704,15 +811,51 @@ uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, in
     G.inv_reg = 1.0f / reg;
     G.g_host = grad_out;
     G.g_dev = grad_out_dev;
-    const dim3 gg((M + GB - 1) / GB, (N + GB - 1) / GB);
+    G.B = Bt;
+    const dim3 gg((M + GB - 1) / GB, (N + GB - 1) / GB, batch);
     bw_gemm_kernel<<<gg, GT, 0, s>>>(G);
     if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
-    bw_scale_kernel<<<std::max(1, std::min((std::max(N, M) + 255) / 256, sms * 4)), 256, 0, s>>>(
-        da, N, db, M, grad_out, grad_out_dev);
+    bw_scale_kernel<<<dim3(std::max(1, std::min((std::max(N, M) + 255) / 256, per_prob)), batch),
+                      256, 0, s>>>(da, N, db, M, grad_out, grad_out_dev);
     if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
     count_launch(2);
   }
   return UOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uot_status uot_sinkhorn_backward(const float* K, int64_t ldk, const float* C, int64_t ldc,
+                                 const float* a, const float* b, int64_t n, int64_t m, float reg,
+                                 float reg_m, int32_t iters, const void* hist, size_t hist_bytes,
+                                 double grad_out, const double* grad_out_dev, float* dC,
+                                 int64_t lddc, float* da, float* db, void* workspace,
+                                 size_t ws_bytes, const uot_options* opt, void* stream) {
+  return backward_run(1, K, ldk, 0, C, ldc, 0, a, b, n, m, reg, reg_m, iters, hist, hist_bytes, 0,
+                      grad_out, grad_out_dev, dC, lddc, 0, da, db, workspace, ws_bytes, opt,
+                      stream);
+}
+
+size_t uot_backward_batch_workspace_size(int32_t batch, int64_t n, int64_t m, int32_t iters) {
+  const size_t one = uot_backward_workspace_size(n, m, iters);
+  if (one == 0 || batch < 1 || batch > 65535 || one > SIZE_MAX / size_t(batch)) return 0;
+  return one * size_t(batch);
+}
+
+uot_status uot_sinkhorn_backward_batch(int32_t batch, const float* K, int64_t ldk,
+                                       int64_t stride_k, const float* C, int64_t ldc,
+                                       int64_t stride_c, const float* a, const float* b,
+                                       int64_t n, int64_t m, float reg, float reg_m,
+                                       int32_t iters, const void* hist, size_t hist_stride,
+                                       double grad_out, const double* grad_out_dev, float* dC,
+                                       int64_t lddc, int64_t stride_dc, float* da, float* db,
+                                       void* workspace, size_t ws_bytes, const uot_options* opt,
+                                       void* stream) {
+  return backward_run(batch, K, ldk, stride_k, C, ldc, stride_c, a, b, n, m, reg, reg_m, iters,
+                      hist, hist_stride, hist_stride, grad_out, grad_out_dev, dC, lddc, stride_dc,
+                      da, db, workspace, ws_bytes, opt, stream);
 }
 
 }  // extern "C"

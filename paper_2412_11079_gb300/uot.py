@@ -102,6 +102,11 @@ SIGNATURES = {
     "uot_sinkhorn_backward": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _P, _I64, _I64, _F, _F,
                                              _I32, _P, _SZ, _D, _P, _P, _I64, _P, _P, _P, _SZ,
                                              ctypes.POINTER(UotOptions), _P]),
+    "uot_backward_batch_workspace_size": (_SZ, [_I32, _I64, _I64, _I32]),
+    "uot_sinkhorn_backward_batch": (ctypes.c_int, [_I32, _P, _I64, _I64, _P, _I64, _I64, _P, _P,
+                                                   _I64, _I64, _F, _F, _I32, _P, _SZ, _D, _P,
+                                                   _P, _I64, _I64, _P, _P, _P, _SZ,
+                                                   ctypes.POINTER(UotOptions), _P]),
     "uot_sinkhorn_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _I64, _I64, _F, _F, _I32, _D,
                                             ctypes.POINTER(UotOptions), _P,
                                             ctypes.POINTER(UotResult)]),
@@ -172,6 +177,25 @@ def _matrix(x, name):
     if x.dim() != 2 or (x.shape[1] > 1 and x.stride(1) != 1) or x.stride(0) < x.shape[1]:
         raise ValueError(f"{name} must be a row-major 2-D tensor (unit column stride)")
     return x.data_ptr(), int(x.stride(0))
+
+
+def _batch_matrix(x, name):
+    """(pointer, leading dimension, batch stride) of a [batch, rows, cols]
+    tensor with unit column stride."""
+    if not x.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if x.dim() != 3 or (x.shape[2] > 1 and x.stride(2) != 1) or x.stride(1) < x.shape[2]:
+        raise ValueError(f"{name} must be a [batch, rows, cols] tensor with unit column stride")
+    return x.data_ptr(), int(x.stride(1)), int(x.stride(0))
+
+
+def _batch_vector(x, name, batch, length):
+    torch = _torch()
+    if (not x.is_cuda or x.dtype != torch.float32 or tuple(x.shape) != (batch, length)
+            or not x.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA float32 tensor of shape "
+                         f"({batch}, {length})")
+    return x.data_ptr()
 
 
 def _vector(x, name, length):
@@ -591,6 +615,54 @@ def uot_sinkhorn_kform_save(K, a, b, reg: float, reg_m: float, iters: int, U=Non
                                           _stream(stream), None),
            "uot_sinkhorn_kform_save")
     return U, V, hist
+
+
+def grad_hist_batch(batch: int, n: int, m: int, iters: int, device=None):
+    """Histories of `batch` solves for the batched adjoint: a [batch, stride]
+    byte tensor, 256-byte aligned rows (one uot_sinkhorn_kform_save each)."""
+    size = int(load().uot_grad_hist_size(n, m, int(iters)))
+    if size == 0 or batch < 1:
+        raise ValueError("bad problem size")
+    stride = (size + 255) // 256 * 256
+    return workspace_bytes(stride * batch, device).view(batch, stride)
+
+
+def uot_sinkhorn_backward_batch(K, C, a, b, reg: float, reg_m: float, iters: int, hist,
+                                grad_out: float = 1.0, dC=None, da=None, db=None, ws=None,
+                                stream=None, opt: UotOptions | None = None, grad_out_dev=None):
+    """Adjoint of `batch` solves of one shape in one set of launches (one per
+    reverse step for the whole batch).  K, C, dC: [batch, n, m] (unit column
+    stride); a, da: [batch, n]; b, db: [batch, m]; hist: [batch, stride]
+    bytes from grad_hist_batch; grad_out_dev: None or a CUDA float64 tensor
+    of `batch` per-problem factors."""
+    torch = _torch()
+    B, n, m = K.shape
+    gdev = None
+    if grad_out_dev is not None:
+        if (not grad_out_dev.is_cuda or grad_out_dev.dtype != torch.float64
+                or grad_out_dev.numel() != B or not grad_out_dev.is_contiguous()):
+            raise ValueError("grad_out_dev must be a contiguous CUDA float64 tensor of batch "
+                             "entries")
+        gdev = grad_out_dev.data_ptr()
+    if dC is None:
+        dC = torch.empty((B, n, (m + 3) // 4 * 4), device=K.device)[:, :, :m]
+    da = torch.empty((B, n), device=K.device) if da is None else da
+    db = torch.empty((B, m), device=K.device) if db is None else db
+    if ws is None:
+        ws = workspace_bytes(int(load().uot_backward_batch_workspace_size(B, n, m, int(iters))),
+                             K.device)
+    if hist.dim() != 2 or hist.shape[0] != B or hist.dtype != torch.uint8 or hist.stride(1) != 1:
+        raise ValueError("hist must be a [batch, stride] uint8 tensor (grad_hist_batch)")
+    kp, ldk, sk = _batch_matrix(K, "K")
+    cp, ldc, sc = _batch_matrix(C, "C")
+    gp, ldd, sd = _batch_matrix(dC, "dC")
+    _check(load().uot_sinkhorn_backward_batch(
+        B, kp, ldk, sk, cp, ldc, sc, _batch_vector(a, "a", B, n), _batch_vector(b, "b", B, m),
+        n, m, float(reg), float(reg_m), int(iters), hist.data_ptr(), int(hist.stride(0)),
+        float(grad_out), gdev, gp, ldd, sd, _batch_vector(da, "da", B, n),
+        _batch_vector(db, "db", B, m), ws.data_ptr(), ws.numel(),
+        ctypes.byref(opt) if opt else None, _stream(stream)), "uot_sinkhorn_backward_batch")
+    return dC, da, db
 
 
 def uot_sinkhorn_backward(K, C, a, b, reg: float, reg_m: float, iters: int, hist,

@@ -195,3 +195,27 @@ def test_size_limits(lib):
     assert lib.uot_workspace_size(4, 1 << 30, None) > 0
     for n, m in ((0, 4), (4, 0), ((1 << 30) + 1, 4), (4, (1 << 30) + 1), (-1, 4)):
         assert lib.uot_workspace_size(n, m, None) == 0
+
+
+def test_backward_batch_validation(lib):
+    """The batched adjoint refuses bad batches, overlapping problems and a
+    short workspace before touching the device (fake, aligned pointers)."""
+    from paper_2412_11079_gb300 import uot
+    n, m, T = 64, 96, 5
+    one = int(lib.uot_backward_workspace_size(n, m, T))
+    assert one > 0 and int(lib.uot_backward_batch_workspace_size(3, n, m, T)) == 3 * one
+    assert int(lib.uot_backward_batch_workspace_size(0, n, m, T)) == 0
+    hs = (int(lib.uot_grad_hist_size(n, m, T)) + 255) // 256 * 256
+    P = ctypes.c_void_p(1 << 20)  # 256-byte aligned, never dereferenced
+
+    def call(batch, sk=n * m, sc=n * m, sd=n * m, hstride=hs, ws=3 * one):
+        return lib.uot_sinkhorn_backward_batch(batch, P, m, sk, P, m, sc, P, P, n, m, 0.1, 0.7,
+                                               T, P, hstride, 1.0, None, P, m, sd, P, P, P, ws,
+                                               None, None)
+    assert call(0) == uot.UOT_ERR_INVALID_ARG
+    assert call(70000) == uot.UOT_ERR_INVALID_ARG
+    assert call(3, sk=n * m - 1) == uot.UOT_ERR_INVALID_ARG       # problems overlap
+    assert call(3, sd=n * m + 2) == uot.UOT_ERR_INVALID_ARG       # dC rows lose alignment
+    assert call(3, hstride=hs - 256) == uot.UOT_ERR_INVALID_ARG   # history too short
+    assert call(3, hstride=hs + 8) == uot.UOT_ERR_INVALID_ARG     # history misaligned
+    assert call(3, ws=3 * one - 1) == uot.UOT_ERR_WORKSPACE

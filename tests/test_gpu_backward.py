@@ -191,3 +191,67 @@ def test_backward_takes_grad_out_on_the_device(ag):
     close(dC.double().cpu().numpy(), -1.5 * rdC, mC)
     close(da.double().cpu().numpy(), -1.5 * rda, ma)
     close(db.double().cpu().numpy(), -1.5 * rdb, mb)
+
+
+def batched_case(seeds, n, m, iters, reg=0.1, reg_m=0.7):
+    """Problems of one shape and parameters (a uniform batch), K with a padded
+    leading dimension; the forward solves recorded per problem."""
+    from paper_2412_11079_gb300 import uot
+    probs = [workloads.gauss_normalised(s, n, m, 16, reg, reg_m, iters, 1.0, 1.5, "uniform")
+             for s in seeds]
+    B, ld = len(probs), (m + 3) // 4 * 4 + 4
+    C = torch.stack([torch.from_numpy(p.C) for p in probs]).cuda()
+    a = torch.stack([torch.from_numpy(p.a) for p in probs]).cuda()
+    b = torch.stack([torch.from_numpy(p.b) for p in probs]).cuda()
+    K = torch.empty((B, n, ld), device="cuda")[:, :, :m]
+    hist = uot.grad_hist_batch(B, n, m, iters)
+    for k, p in enumerate(probs):
+        uot.uot_init_kernel(C[k], K[k], p.reg)
+        uot.uot_sinkhorn_kform_save(K[k], a[k], b[k], p.reg, p.reg_m, iters, hist=hist[k])
+    return probs, C, a, b, K, hist
+
+
+def test_batched_adjoint_matches_oracle_per_problem(ag):
+    """Three problems in one batched adjoint (one reverse launch per step for
+    all three): M not a multiple of 4, padded K, per-problem device factors
+    times the host grad_out; each problem against the oracle's gradient."""
+    from paper_2412_11079_gb300 import uot
+    probs, C, a, b, K, hist = batched_case([11, 12, 13], 300, 517, 25)
+    g = torch.tensor([1.0, -2.0, 3.0], dtype=torch.float64, device="cuda")
+    dC, da, db = uot.uot_sinkhorn_backward_batch(K, C, a, b, probs[0].reg, probs[0].reg_m, 25,
+                                                 hist, 0.5, grad_out_dev=g)
+    torch.cuda.synchronize()
+    for k, p in enumerate(probs):
+        f = 0.5 * float(g[k])
+        _, rdC, rda, rdb = oracle.sinkhorn_grad(p.C, p.a, p.b, p.reg, p.reg_m, p.iters)
+        mC, ma, mb = magnitudes(p, scale=abs(f))
+        close(dC[k].double().cpu().numpy(), f * rdC, mC)
+        close(da[k].double().cpu().numpy(), f * rda, ma)
+        close(db[k].double().cpu().numpy(), f * rdb, mb)
+
+
+def test_batched_adjoint_workload_geometry(ag):
+    """32 problems of 2048^2, the differentiation workload's batch (19 CTAs
+    per problem in a reverse launch, chunks of 64 rows and a ragged last
+    block): the first and last problems against the oracle's adjoint at 6
+    iterations, every problem against its own single-problem adjoint."""
+    from paper_2412_11079_gb300 import uot
+    iters = 6
+    probs, C, a, b, K, hist = batched_case(list(range(100, 132)), 2048, 2048, iters, 0.05, 1.0)
+    dC, da, db = uot.uot_sinkhorn_backward_batch(K, C, a, b, 0.05, 1.0, iters, hist)
+    torch.cuda.synchronize()
+    for k in (0, 31):
+        p = probs[k]
+        _, rdC, rda, rdb = oracle.sinkhorn_grad(p.C, p.a, p.b, p.reg, p.reg_m, p.iters)
+        mC, ma, mb = magnitudes(p)
+        close(dC[k].double().cpu().numpy(), rdC, mC)
+        close(da[k].double().cpu().numpy(), rda, ma)
+        close(db[k].double().cpu().numpy(), rdb, mb)
+    for k in range(32):
+        sC, sa, sb = uot.uot_sinkhorn_backward(K[k], C[k], a[k], b[k], 0.05, 1.0, iters, hist[k])
+        torch.cuda.synchronize()
+        # same arithmetic up to the order of the atomic column sums
+        scale = float(sC.abs().max())
+        assert float((dC[k] - sC).abs().max()) <= 1e-5 * scale
+        assert float((da[k] - sa).abs().max()) <= 1e-5 * float(sa.abs().max())
+        assert float((db[k] - sb).abs().max()) <= 1e-5 * float(sb.abs().max())
