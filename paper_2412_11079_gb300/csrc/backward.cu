@@ -47,6 +47,16 @@ struct BwBatch {
   size_t sH, sW;       // bytes between problems' histories and workspaces
 };
 
+// Programmatic dependent launch: a reverse step may start while the
+// previous one drains; it waits for that grid (complete, memory visible)
+// before it touches the adjoint state.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void allow_dependent_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <typename P>
 __device__ __forceinline__ P* at_bytes(P* x, size_t off) {  // x advanced by off bytes
   return reinterpret_cast<P*>(reinterpret_cast<uintptr_t>(x) + off);
@@ -130,11 +140,10 @@ __global__ void __launch_bounds__(THREADS, (512 / THREADS > 1 ? 512 / THREADS : 
   float* Aq = at_bytes(p.Aq, ow);
   float* Az = at_bytes(p.Az, ow);
   Control* ctl = at_bytes(p.ctl, ow);
-  const float qscale =
-      ldexpf(1.0f, -gauge_exponent(p.t, float(*at_bytes(p.log2k, oh))));
   const uint32_t copy_bytes = uint32_t((size_t(m) * 4) & ~size_t(15));
   uint32_t st = 0;
 
+  allow_dependent_launch();  // the next step's CTAs fill SMs as this grid's leave
   if (tid == 0) {
     for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
     fence_mbar_init();
@@ -159,7 +168,10 @@ __global__ void __launch_bounds__(THREADS, (512 / THREADS > 1 ? 512 / THREADS : 
     armed = q + 1;
   };
   if (tid == 0)
-    for (int q = 0; q < stages; ++q) arm(q);
+    for (int q = 0; q < stages; ++q) arm(q);  // K is read-only: fetched before the wait
+  grid_dependency_wait();
+  const float qscale =
+      ldexpf(1.0f, -gauge_exponent(p.t, float(*at_bytes(p.log2k, oh))));
 
   // Column step: G = (1 - fi) G + R^T z of the previous step, w = -fi G / c_t,
   // db += fi G / b; the CTA that owns column j (j / ceil(m / cpp) == its
@@ -359,49 +371,60 @@ __global__ void __launch_bounds__(TB) bw_zero_kernel(unsigned char* ws, size_t b
     z[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// dl = P_T * C with P_T = (U_i K_ij) V_j; F = rowsum(dl) (one warp per row;
-// grid.y = problem).
-__global__ void __launch_bounds__(TB) bw_init_kernel(const float* K, int64_t ldk, const float* C,
-                                                     int64_t ldc, const float* U, const float* V,
-                                                     float* D, int64_t ldd, int n, int m,
-                                                     float* F, float* da, BwBatch B) {
-  const int k = blockIdx.y;
+// The adjoint's start, one read of K and C: dl = P_T * C with P_T =
+// (U_i K_ij) V_j (not stored: the final contraction forms it again),
+// F = rowsum(dl) and G0 = colsum(dl), da = 0.  A thread takes four
+// consecutive columns of a block of rows: its column sums stay in registers
+// (one atomic each at the end) and each row's sum is reduced over the CTA
+// (one atomic per row and CTA).  grid = (column blocks, row blocks, problem).
+constexpr int ST_ROWS = 32;
+__global__ void __launch_bounds__(TB) bw_start_kernel(const float* K, int64_t ldk, const float* C,
+                                                      int64_t ldc, const float* U, const float* V,
+                                                      int n, int m, float* F, float* G0,
+                                                      float* da, BwBatch B) {
+  __shared__ float part[TB / 32][ST_ROWS];
+  const int k = blockIdx.z;
   K += int64_t(k) * B.sK;
   C += int64_t(k) * B.sC;
-  D += int64_t(k) * B.sD;
   U = at_bytes(U, size_t(k) * B.sH);
   V = at_bytes(V, size_t(k) * B.sH);
   F = at_bytes(F, size_t(k) * B.sW);
+  G0 = at_bytes(G0, size_t(k) * B.sW);
   da += int64_t(k) * n;
-  const int warp = (blockIdx.x * TB + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int nw = (gridDim.x * TB) >> 5;
-  for (int i = warp; i < n; i += nw) {
-    float s = 0.0f;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = (blockIdx.x * TB + threadIdx.x) * 4;
+  const int r0 = blockIdx.y * ST_ROWS, r1 = min(n, r0 + ST_ROWS);
+  float v[4], g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) v[e] = j + e < m ? V[j + e] : 0.0f;
+  for (int i = r0; i < r1; ++i) {
     const float u = U[i];
-    for (int j = lane; j < m; j += 32) {
-      const float dl = (u * K[int64_t(i) * ldk + j]) * V[j] * C[int64_t(i) * ldc + j];
-      D[int64_t(i) * ldd + j] = dl;
-      s += dl;
+    float s = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (j + e < m) {
+        const float dl = (u * __ldg(K + int64_t(i) * ldk + j + e)) * v[e] *
+                         __ldg(C + int64_t(i) * ldc + j + e);
+        g[e] += dl;
+        s += dl;
+      }
     }
     s = warp_sum(s);
-    if (lane == 0) {
-      F[i] = s;
-      da[i] = 0.0f;
+    if (lane == 0) part[warp][i - r0] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int i = r0 + lane; i < r1; i += 32) {
+      float s = 0.0f;
+#pragma unroll
+      for (int w = 0; w < TB / 32; ++w) s += part[w][i - r0];
+      atomicAdd(F + i, s);
+      if (blockIdx.x == 0) da[i] = 0.0f;
     }
   }
-}
-
-// G0 = colsum(dl): a column per thread over a stride of rows, then atomics
-// (grid.z = problem).
-__global__ void __launch_bounds__(TB) bw_colsum_kernel(const float* D, int64_t ldd, int n, int m,
-                                                       float* G0, BwBatch B) {
-  const int j = blockIdx.x * TB + threadIdx.x;
-  if (j >= m) return;
-  D += int64_t(blockIdx.z) * B.sD;
-  G0 = at_bytes(G0, size_t(blockIdx.z) * B.sW);
-  float s = 0.0f;
-  for (int i = blockIdx.y; i < n; i += gridDim.y) s += D[int64_t(i) * ldd + j];
-  atomicAdd(G0 + j, s);
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    if (j + e < m && r1 > r0) atomicAdd(G0 + j + e, g[e]);
 }
 
 // The final contraction: acc = A B^T over the 2T recorded step vectors
@@ -409,8 +432,13 @@ __global__ void __launch_bounds__(TB) bw_colsum_kernel(const float* D, int64_t l
 //     dl = P_T * C + K * acc,   dC = g (P_T - dl / reg),
 // with g = grad_out times the optional device scalar (read here, so the
 // caller need not synchronise).  FP32 on the CUDA cores (the depth-2T sum
-// needs FP32 accuracy): 128 x 128 tiles, 16 steps of depth per stage in
-// shared memory, 8 x 8 outputs per thread.
+// needs FP32 accuracy): 128 x 128 tiles of 256 threads, 8 x 8 outputs per
+// thread (rows ty*4 + {0..3} and 64 + ty*4 + {0..3}, columns likewise with
+// tx, so the 16-byte shared loads of a warp hit distinct banks), slabs of 16
+// depth steps in two shared buffers: the next slab is fetched into
+// registers (16-byte loads) while the current one is used, one barrier per
+// slab, and the FMAs packed in pairs.  The step vectors are padded to 128
+// entries (the workspace layout), so a tile's loads stay inside them.
 constexpr int GB = 128, GKD = 16, GT = 256;
 
 struct BwGemmArgs {
@@ -434,7 +462,7 @@ struct BwGemmArgs {
   BwBatch B;
 };
 
-__global__ void __launch_bounds__(GT) bw_gemm_kernel(BwGemmArgs p) {
+__global__ void __launch_bounds__(GT, 2) bw_gemm_kernel(BwGemmArgs p) {
   {  // problem blockIdx.z of the batch
     const int k = blockIdx.z;
     const size_t oh = size_t(k) * p.B.sH, ow = size_t(k) * p.B.sW;
@@ -449,68 +477,83 @@ __global__ void __launch_bounds__(GT) bw_gemm_kernel(BwGemmArgs p) {
     p.Bw = at_bytes(p.Bw, ow);
     if (p.g_dev) p.g_dev += k;
   }
-  __shared__ __align__(16) float As[GKD][GB];
-  __shared__ __align__(16) float Bs[GKD][GB];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  __shared__ __align__(16) float As[2][GKD][GB];
+  __shared__ __align__(16) float Bs[2][GKD][GB];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const int i0 = blockIdx.y * GB, j0 = blockIdx.x * GB;
   const int S = 2 * p.T;
-  float acc[8][8];
+  // Loader: float4 number f = tid + 256 h (h = 0, 1) of a slab's 16 x 32.
+  float4 ra[2], rb[2];
+  auto fetch = [&](int s0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int f = tid + h * GT, row = f / 32, c4 = (f % 32) * 4;
+      const int sidx = s0 + row;
+      ra[h] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      rb[h] = ra[h];
+      if (sidx < p.T) {
+        ra[h] = __ldg(reinterpret_cast<const float4*>(p.Aq + sidx * p.sn + i0 + c4));
+        rb[h] = __ldg(reinterpret_cast<const float4*>(p.Bw + sidx * p.sm + j0 + c4));
+      } else if (sidx < S) {
+        ra[h] = __ldg(reinterpret_cast<const float4*>(p.Az + (sidx - p.T) * p.sn + i0 + c4));
+        rb[h] = __ldg(reinterpret_cast<const float4*>(p.Vh + (sidx - p.T) * p.sv + j0 + c4));
+      }
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int f = tid + h * GT, row = f / 32, c4 = (f % 32) * 4;
+      *reinterpret_cast<float4*>(&As[buf][row][c4]) = ra[h];
+      *reinterpret_cast<float4*>(&Bs[buf][row][c4]) = rb[h];
+    }
+  };
+  float2 acc[8][4];  // rows r, column pairs
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c] = 0.0f;
-  const int lk = threadIdx.x / 16, l8 = (threadIdx.x % 16) * 8;  // loader: depth row, 8 entries
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.0f, 0.0f);
+  if (S > 0) {
+    fetch(0);
+    stash(0);
+  }
+  __syncthreads();
+  int cur = 0;
   for (int s0 = 0; s0 < S; s0 += GKD) {
-    {
-      const int sidx = s0 + lk;
-      const float* arow = nullptr;
-      const float* brow = nullptr;
-      if (sidx < p.T) {
-        arow = p.Aq + sidx * p.sn;
-        brow = p.Bw + sidx * p.sm;
-      } else if (sidx < S) {
-        arow = p.Az + (sidx - p.T) * p.sn;
-        brow = p.Vh + (sidx - p.T) * p.sv;
-      }
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int i = i0 + l8 + e, j = j0 + l8 + e;
-        As[lk][l8 + e] = (arow && i < p.n) ? __ldg(arow + i) : 0.0f;
-        Bs[lk][l8 + e] = (brow && j < p.m) ? __ldg(brow + j) : 0.0f;
-      }
-    }
-    __syncthreads();
+    const bool more = s0 + GKD < S;
+    if (more) fetch(s0 + GKD);
 #pragma unroll
     for (int kk = 0; kk < GKD; ++kk) {
-      float a[8], b[8];
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
-      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
-      a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
-      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
-      b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float2 b[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w),
+                           make_float2(b1.x, b1.y), make_float2(b1.z, b1.w)};
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        for (int c = 0; c < 4; ++c) acc[r][c] = ffma2(make_float2(a[r], a[r]), b[c], acc[r][c]);
     }
+    if (more) stash(cur ^ 1);
     __syncthreads();
+    cur ^= 1;
   }
   const float g = float(p.g_dev ? p.g_host * *p.g_dev : p.g_host);
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
-    const int i = i0 + ty * 8 + r;
+    const int i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4);
     if (i >= p.n) continue;
     const float u = p.UT[i];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      const int j = j0 + tx * 8 + c;
+      const int j = j0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + c - 4);
       if (j >= p.m) continue;
       const float k = p.K[int64_t(i) * p.ldk + j];
       const float P = (u * k) * p.VT[j];
-      const float dl = fmaf(k, acc[r][c], P * p.C[int64_t(i) * p.ldc + j]);
+      const float a = (c & 1) ? acc[r][c / 2].y : acc[r][c / 2].x;
+      const float dl = fmaf(k, a, P * p.C[int64_t(i) * p.ldc + j]);
       p.D[int64_t(i) * p.ldd + j] = g * (P - dl * p.inv_reg);
     }
   }
@@ -577,8 +620,8 @@ struct BwLayout {
 };
 BwLayout bw_layout(int64_t n, int64_t m, int T) {
   BwLayout L{};
-  L.npad = size_t((n + 63) & ~int64_t(63));
-  L.mpad = size_t((m + 63) & ~int64_t(63));
+  L.npad = size_t((n + 127) & ~int64_t(127));  // step vectors of whole 128-entry tiles
+  L.mpad = size_t((m + 127) & ~int64_t(127));
   const size_t npad = L.npad * 4, mpad = L.mpad * 4;
   size_t off = 0;
   L.ctl = off; off = align256(off + sizeof(Control));
@@ -696,16 +739,11 @@ uot_status backward_run(int32_t batch, const float* K, int64_t ldk, int64_t sK, 
   bw_zero_kernel<<<dim3(std::max(1, std::min(per_prob, int(L.state_end / (16 * TB)) + 1)), batch),
                    TB, 0, s>>>(ws, L.state_end, L.total);
   if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
-  bw_init_kernel<<<dim3(per_prob, batch), TB, 0, s>>>(K, ldk, C, ldc, U_t(T), V_t(T), dC, lddc,
-                                                      N, M, F, da, Bt);
+  if ((N + ST_ROWS - 1) / ST_ROWS > 65535) return UOT_ERR_UNSUPPORTED;
+  bw_start_kernel<<<dim3((M + 4 * TB - 1) / (4 * TB), (N + ST_ROWS - 1) / ST_ROWS, batch), TB, 0,
+                    s>>>(K, ldk, C, ldc, U_t(T), V_t(T), N, M, F, G0, da, Bt);
   if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
-  {
-    const int gx = (M + TB - 1) / TB;
-    const int gy = std::max(1, std::min(std::min(N, 65535), (per_prob + gx - 1) / gx));
-    bw_colsum_kernel<<<dim3(gx, gy, batch), TB, 0, s>>>(dC, lddc, N, M, G0, Bt);
-    if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
-  }
-  count_launch(3);
+  count_launch(2);
   if (T == 0 && cudaMemsetAsync(db, 0, size_t(batch) * size_t(M) * 4, s) != cudaSuccess)
     return UOT_ERR_CUDA;
 
@@ -752,7 +790,7 @@ uot_status backward_run(int32_t batch, const float* K, int64_t ldk, int64_t sK, 
   A.ldk = ldk;
   A.n = N;
   A.m = M;
-  A.mpad = int((m + 63) & ~int64_t(63));
+  A.mpad = int(L.mpad);
   A.cpp = cpp;
   A.a = a;
   A.b = b;
@@ -784,8 +822,17 @@ uot_status backward_run(int32_t batch, const float* K, int64_t ldk, int64_t sK, 
     A.Az = Az + size_t(t - 1) * L.npad;
     A.Bw = Bw + size_t(t - 1) * L.mpad;
     void* kargs[] = {&A};
-    if (cudaLaunchKernel(fn, dim3(batch * cpp), dim3(e.threads), kargs, smem, s) != cudaSuccess)
-      return UOT_ERR_CUDA;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(batch * cpp);
+    cfg.blockDim = dim3(e.threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelExC(&cfg, fn, kargs) != cudaSuccess) return UOT_ERR_CUDA;
     count_launch();
   }
   {
