@@ -439,15 +439,18 @@ def measure_grad(args, batch: int, n: int, iters: int, steps: int, warmup: int,
             uot.uot_init_kernel(C3[i], K3[i], reg, stream=bs)
             uot.uot_sinkhorn_kform_save(K3[i], a2[i], b2[i], reg, reg_m, iters, U2[i], V2[i],
                                         hist2[i], wss[i], bs, opt)
-            if backward:
+            if backward and per_problem:
                 uot.uot_kform_cost(K3[i], U2[i], V2[i], C3[i], cost[i:i + 1], bs)
-                if per_problem:
-                    uot.uot_sinkhorn_backward(K3[i], C3[i], a2[i], b2[i], reg, reg_m, iters,
-                                              hist2[i], 1.0, dC3[i], da2[i], db2[i], bwss[i],
-                                              bs, bopt)
+                uot.uot_sinkhorn_backward(K3[i], C3[i], a2[i], b2[i], reg, reg_m, iters,
+                                          hist2[i], 1.0, dC3[i], da2[i], db2[i], bwss[i],
+                                          bs, bopt)
         for br in branches:
             s.wait_stream(br)
         if backward and not per_problem:
+            # The costs after the join: a full-grid cost launch on a branch
+            # would hold up the other branches' narrow forward launches.
+            for i in range(B):
+                uot.uot_kform_cost(K3[i], U2[i], V2[i], C3[i], cost[i:i + 1], s)
             uot.uot_sinkhorn_backward_batch(K3, C3, a2, b2, reg, reg_m, iters, hist2, 1.0, dC3,
                                             da2, db2, bws, s)
 
