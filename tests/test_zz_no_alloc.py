@@ -1,6 +1,7 @@
 """uot_sinkhorn_noalloc, the entry point for callers that cannot allocate
 device memory (it runs on a scratch array built into the library), against
-the workspace-taking uot_sinkhorn on the same inputs, through the C ABI.
+the workspace-taking uot_sinkhorn on the same inputs and against the FP64
+oracle, through the C ABI.
 
 Two calls in a row with different shapes also check that the array's stale
 contents from the first call do not leak into the second.  This file is
@@ -62,6 +63,19 @@ def test_noalloc_matches_workspace_entry_point_twice(uot):
         assert res.dev_status == ref.dev_status == 0
         assert res.iters_done == ref.iters_done
         assert rel_err(got_plan, ref_plan) <= FP32_TOL
+
+
+def test_noalloc_matches_the_oracle(uot):
+    """The no-allocation entry point against the FP64 oracle of the rule
+    (Section 2.1), element by element at the FP32 tolerance: a ragged shape
+    over several tiles, 30 iterations."""
+    import oracle
+    p = workloads.uniform2d(seed=34, n=257, m=333, reg=0.08, reg_m=0.9, iters=30)
+    _, res, _, got_plan = solve_both(uot, p)
+    want = oracle.sinkhorn(oracle.init_plan(p.C, p.reg), p.a, p.b, p.reg, p.reg_m, p.iters)
+    assert res.dev_status == 0 and want.status == 0
+    assert res.iters_done == p.iters
+    assert rel_err(got_plan, want.plan) <= FP32_TOL
 
 
 def test_noalloc_rejects_problems_beyond_the_static_scratch(uot):
