@@ -742,8 +742,8 @@ def main():
     ap.add_argument("--grad-check-iters", type=int, default=5)
     ap.add_argument("--no-extra", action="store_true",
                     help="default run: skip the precision, batched and gradient comparisons")
-    ap.add_argument("--grad-streams", type=int, default=16)
-    ap.add_argument("--grad-max-ctas", type=int, default=80)
+    ap.add_argument("--grad-streams", type=int, default=32)
+    ap.add_argument("--grad-max-ctas", type=int, default=24)
     ap.add_argument("--grad-bwd-max-ctas", type=int, default=80,
                     help="CTA cap of the per-problem adjoint's launches")
     ap.add_argument("--grad-backward", choices=["batched", "per-problem"], default="batched")
