@@ -61,12 +61,14 @@ __global__ void __launch_bounds__(TB) mode2_kernel(const float* M, int n2, int n
 
 // gamma_k = (c_k / sum_j beta_j M_jk)^fi and the pending factor
 // beta_j gamma_k of every unfolded column for the next pass.  A CTA takes 32
-// values of k (one per lane); its 8 warps add every 8th j, and one warp adds
-// the 8 partial sums in warp order; then every warp writes 32 consecutive
-// pending factors per row j.
-constexpr int M3_WARPS = TB / 32;
+// values of k (one per lane); its 32 warps add every 32nd j (a short chain
+// of loads per warp: there are only n3 / 32 CTAs), and one warp adds the
+// partial sums in warp order; then every warp writes 32 consecutive pending
+// factors per row j.
+constexpr int M3_THREADS = 1024;
+constexpr int M3_WARPS = M3_THREADS / 32;
 
-__global__ void __launch_bounds__(TB) mode3_kernel(const float* M, int n2, int n3, const float* c,
+__global__ void __launch_bounds__(M3_THREADS) mode3_kernel(const float* M, int n2, int n3, const float* c,
                                                    float fi, const float* beta, float* gamma,
                                                    float* pending, Control* ctl, int t) {
   __shared__ float part[M3_WARPS][32];
@@ -200,7 +202,7 @@ uot_status uot_sinkhorn_tensor3(void* P, int64_t n1, int64_t n2, int64_t n3, con
       if (fused_launch(false, k, cs, grid, smem, tma, A, s) != cudaSuccess) return UOT_ERR_CUDA;
       mode2_kernel<<<g2, TB, 0, s>>>(cnext, N2, N3, b, fi, beta2, ctl);
       if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
-      mode3_kernel<<<g3, TB, 0, s>>>(cnext, N2, N3, c, fi, beta2, gamma3, pending, ctl, t);
+      mode3_kernel<<<g3, M3_THREADS, 0, s>>>(cnext, N2, N3, c, fi, beta2, gamma3, pending, ctl, t);
       if (cudaGetLastError() != cudaSuccess) return UOT_ERR_CUDA;
       count_launch(2);
     }
