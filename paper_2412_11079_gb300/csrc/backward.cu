@@ -601,7 +601,9 @@ struct BwEntry {
 // Four vectors per thread (four warps for rows of 2048 columns, four CTAs
 // per SM): a reverse step's CTA barrier per row is cheapest with few warps,
 // and the per-row latency is hidden by CTAs side by side rather than by wider
-// CTAs (512 x 1: 69 ms, 256 x 2: 55 ms, 128 x 4: 48 ms per gradient step).
+// CTAs (measured with one launch per problem and step: 512 x 1 69 ms,
+// 256 x 2 55 ms, 128 x 4 48 ms per gradient step; a fifth CTA per SM, at
+// 96 registers, made the batched launches slower).
 const BwEntry kBw[] = {BW_ENTRY(512, 4), BW_ENTRY(256, 4), BW_ENTRY(128, 4),
                        BW_ENTRY(128, 2), BW_ENTRY(64, 2),  BW_ENTRY(32, 2)};
 constexpr int kBwNum = int(sizeof(kBw) / sizeof(kBw[0]));
